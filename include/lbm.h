@@ -1,0 +1,158 @@
+/*
+ * lbm.h - C ABI of the GB300 PML + outer-boundary thermal lattice Boltzmann step.
+ *
+ * Method: Klass, Gabbana, Bartel, "Perfectly Matched Layers and Characteristic Boundaries in
+ * Lattice Boltzmann: Accuracy vs. Cost" (arXiv 2504.20169).
+ *   - lattice BGK step, Eq. (lbe); moments, Eq. (macro); Hermite equilibria Eqs. (feq-2..4),
+ *     with the fourth-order mixed temperature term read as (c^2 - 6) (the printed (c^2 - 4)
+ *     does not return the density it was built from);
+ *   - PML: Eqs. (decomp-NJ), (PMLCOLL), (PML_ramp), (PMLQ) with the trapezoidal rule, gradients
+ *     Eqs. (FD-dx-center) / (FD-dx-bw);
+ *   - outer boundary: zero gradient, Eq. (zg-bc), or the characteristic BC of Sec. 4
+ *     (Eqs. NSF-CHAR, PNR, thermal_LODI_macro_evo, thermal_CBC_macro_evo, CBC-Relax) with
+ *     non-equilibrium extrapolation.
+ *
+ * Geometry. Bulk nx x ny nodes; W PML layers on every side give the fluid region F of
+ * Lx x Ly = (nx + 2W) x (ny + 2W) nodes (Fig. 2); M boundary layers outside F (M = 3 for D2Q37
+ * and D2Q17, 1 for D2Q9) hold the boundary nodes x_(b,j) of Sec. 4. Field arrays passed through
+ * this ABI are float64, row-major with y outer: element (y, x) at index y * Lx + x over F, or
+ * y * nx + x over the bulk.
+ *
+ * Units. Normalized Hermite units of the equilibria: c_s = 1, reference temperature 1, velocity
+ * in units of c_s. The lattice moves e_i (integer) nodes per step with xi_i = r e_i, so one node
+ * is r normalized lengths; lbm_lattice_info returns r.
+ *
+ * Conventions. Every call returns an lbm_status and never aborts. The library owns all device
+ * memory of a context; the caller owns every pointer it passes. Work is queued on the context's
+ * CUDA stream; calls that return host data synchronize that stream. A context is not
+ * thread-safe; separate contexts are independent. After LBM_EUNSTABLE the context is poisoned:
+ * lbm_moments, lbm_export_populations, lbm_last_error and lbm_destroy still work.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,     /* invalid argument or combination; nothing allocated */
+  LBM_ENOMEM = 2,     /* device or pinned allocation failed */
+  LBM_ECUDA = 3,      /* a CUDA call failed; lbm_last_error has the message */
+  LBM_EUNSTABLE = 4,  /* a non-finite or non-positive density / temperature was produced */
+  LBM_ETIMEOUT = 5,   /* reserved for bounded device-side waits */
+  LBM_ESTATE = 6      /* call not valid in the context's state (e.g. step before init) */
+} lbm_status;
+
+/* Velocity stencils of Sec. 2 (Fig. 1): q velocities; equilibrium order 2 / 3 / 4. */
+typedef enum { LBM_D2Q9 = 9, LBM_D2Q17 = 17, LBM_D2Q37 = 37 } lbm_stencil;
+
+/* Outer boundary of the PML-extended grid. PERIODIC is the fully periodic reference mode of
+ * Sec. 5 ("Reference Simulation") and requires pml_width == 0. */
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_ZG = 1, LBM_BC_NRBC = 2 } lbm_bc_kind;
+
+/* Characteristic BC variant per edge (Sec. 4, Sec. 5.2):
+ * PNR_LODI   incoming amplitudes zero, Eq. (PNR), LODI evolution Eq. (thermal_LODI_macro_evo);
+ * CBC_RELAX  incoming amplitudes relaxed against the transverse terms, Eq. (CBC-Relax), with
+ *            the CBC evolution Eq. (thermal_CBC_macro_evo). Reading of the printed sign: the
+ *            incoming amplitude is relax_sign * (1 - beta) * T_inc, relax_sign = -1 by default
+ *            (beta = 1 leaves the transverse term, beta = 0 freezes the incoming wave). */
+typedef enum { LBM_NRBC_PNR_LODI = 0, LBM_NRBC_CBC_RELAX = 1 } lbm_nrbc_variant;
+
+typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1 } lbm_precision;
+
+typedef struct { int nx, ny; } lbm_grid;
+
+/* Eq. (PML_ramp): sigma = sigma_max (i / W)^power on PML layer i = 1..W (power 2 in the
+ * paper). Corner layers use i = max(i_x, i_y). */
+typedef struct { double sigma_max; int power; } lbm_sigma_profile;
+
+typedef struct {
+  int edge[4];                  /* lbm_nrbc_variant for the W, E, S, N edges               */
+  double beta;                  /* relaxation Mach number "Ma" of Eq. (CBC-Relax)            */
+  double relax_sign;            /* -1 (default reading) or +1 (as printed); 0 means -1      */
+  double rho0, u0x, u0y, T0;    /* mean state: f_eq_bar of the PML (Eq. decomp-NJ)          */
+} lbm_bc_params;
+
+/* Create a context. tau > 1/2 (tau = +INFINITY gives collisionless free streaming);
+ * pml_width 0 or >= 2 (the one-sided gradient reaches two nodes inward); bc_params may be NULL
+ * for the rest state (1, 0, 0, 1) and PNR_LODI on every edge. cuda_stream is a cudaStream_t
+ * (NULL = the legacy default stream). Allocates the populations (2 x q x |grid| values of the
+ * precision), the PML accumulator on the PML and its inner ring, and the boundary targets. On
+ * failure *out is NULL and nothing stays allocated. */
+lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int pml_width,
+                      const lbm_sigma_profile* sigma, lbm_bc_kind bc, const lbm_bc_params* bc_params,
+                      lbm_precision precision, void* cuda_stream, lbm_ctx** out);
+
+/* Initialize from macroscopic fields over F (Lx * Ly float64 each, layout above):
+ * f^0 = f_eq(fields) (Sec. 2), Q^0 = 0, boundary targets = fields at the nearest fluid node.
+ * fields_on_device != 0: the four pointers are device pointers; else host pointers (copied
+ * through the library's staging buffer, synchronizing the stream). */
+lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                    const double* T, int fields_on_device);
+
+/* Advance n >= 0 time steps (collide with PML, stream, boundary). Asynchronous on the
+ * context stream. Returns LBM_EUNSTABLE if an earlier step has already flagged an unphysical
+ * state (the flag lives in mapped host memory and is read without synchronizing). */
+lbm_status lbm_step(lbm_ctx* ctx, int n);
+
+/* Wait for queued work; returns LBM_EUNSTABLE if any step flagged an unphysical state. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Macroscopic fields rho, u_x, u_y, T of the current time level over F (region 1) or the bulk
+ * (region 0), float64, layout above. out_on_device != 0: device pointers. Any output pointer may
+ * be NULL. Synchronizes the stream. */
+lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* ux, double* uy, double* T, int region,
+                       int out_on_device);
+
+/* Conserved totals over F at the current time level, FP64 reduction on the device:
+ * out[0] = sum rho, out[1] = sum rho u_x, out[2] = sum rho u_y, out[3] = sum (1/2) sum_i f_i |xi_i|^2,
+ * out[4] = min rho, out[5] = min T, out[6] = number of non-finite or non-positive rho or T.
+ * out is a host array of 7 doubles. Synchronizes. */
+lbm_status lbm_reduce(lbm_ctx* ctx, double* out);
+
+/* Error sums against reference fields over the bulk (Sec. 5 metrics), FP64 on the device.
+ * ref: four device arrays (rho, u_x, u_y, T) of nx * ny float64. out (host, 12 doubles): for
+ * each field Z in that order, out[3k] = sum (Z - Zref)^2, out[3k+1] = sum Zref^2,
+ * out[3k+2] = sum ((Z - Zref) / Zref)^2 (the square of e_Z). Synchronizes. */
+lbm_status lbm_error_sums(lbm_ctx* ctx, const double* ref_rho, const double* ref_ux,
+                          const double* ref_uy, const double* ref_T, double* out);
+
+/* Velocity set and quadrature derived by the library (Sec. 2). Host-only, needs no GPU.
+ * e: 2*q ints (ex, ey per velocity), w: q doubles, r: scale. Any output may be NULL. */
+lbm_status lbm_lattice_info(lbm_stencil stencil, int* q, int* e, double* w, double* r);
+
+/* Grid description of a context: out[0..7] = nx, ny, W, M, Lx, Ly, q, step count. */
+lbm_status lbm_geometry(const lbm_ctx* ctx, int64_t* out);
+
+/* Debug / checkpoint: the stored post-collision populations of the last completed step (or
+ * of the initial collision) on the whole grid G = (Lx + 2M) x (Ly + 2M), as float64 absolute
+ * populations, layout [i][gy][gx]; host buffer of q * Gx * Gy doubles. Synchronizes. */
+lbm_status lbm_export_populations(lbm_ctx* ctx, double* host);
+/* Replace the stored post-collision populations (same layout); the PML accumulator and the
+ * boundary targets are left as they are. Intended for bit-exact streaming tests. */
+lbm_status lbm_import_populations(lbm_ctx* ctx, const double* host);
+
+/* Full checkpoint of a context (populations, PML accumulator, boundary targets and moments,
+ * step count) into a host buffer. lbm_checkpoint_size gives the byte count. A context restored
+ * with lbm_restore into an identically created context continues bit-identically. */
+lbm_status lbm_checkpoint_size(const lbm_ctx* ctx, size_t* bytes);
+lbm_status lbm_checkpoint(lbm_ctx* ctx, void* host, size_t bytes);
+lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes);
+
+/* Last error message of the context (or of the last failed lbm_create when ctx is NULL). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Release everything; NULL is allowed. */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,642 @@
+// C ABI of liblbm (include/lbm.h): context management, validation, the quadrature of Sec. 2,
+// and the host-side sequencing of the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// --------------------------------------------------------------------------------------------
+// Gauss-Hermite rule of a stencil (Sec. 2): one weight per velocity shell and the scale r of
+// xi_i = r e_i such that sum_i w_i xi_x^p xi_y^q equals the unit-Gaussian moment
+// (p-1)!!(q-1)!! for every even pair p >= q with p + q below the quadrature degree. Solved by
+// Newton's method on the square system in (weights, r), started from a least-squares fit.
+// --------------------------------------------------------------------------------------------
+long double odd_df(int n) {
+  long double v = 1;
+  for (int k = n - 1; k > 0; k -= 2) v *= k;
+  return v;
+}
+
+bool solve_linear(std::vector<long double>& A, std::vector<long double>& b, int n) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs((double)A[r * n + c]) > std::fabs((double)A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0) return false;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[piv * n + k]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < n; ++r) {
+      const long double f = A[r * n + c] / A[c * n + c];
+      for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    long double s = b[c];
+    for (int k = c + 1; k < n; ++k) s -= A[c * n + k] * b[k];
+    b[c] = s / A[c * n + c];
+  }
+  return true;
+}
+
+template <class S>
+bool derive_quadrature(int degree, double r0, double* w_dir, double* r_out, std::string& err) {
+  const int ns = S::NSHELL;
+  std::vector<int> cp, cq;
+  for (int s = 0; s < degree; s += 2)
+    for (int p = s; p >= 0; --p) {
+      const int q = s - p;
+      if (p % 2 == 0 && q % 2 == 0 && p >= q) { cp.push_back(p); cq.push_back(q); }
+    }
+  const int ne = (int)cp.size();
+  if (ne != ns + 1) { err = "quadrature: condition count mismatch"; return false; }
+  // lattice moments of every shell: m[k][s] = sum over members of ex^p ey^q
+  std::vector<long double> m(ne * ns, 0);
+  for (int k = 0; k < ne; ++k)
+    for (int s = 0; s < ns; ++s)
+      for (int i = S::shell_first(s); i < S::shell_first(s) + S::shell_size(s); ++i)
+        m[k * ns + s] += std::pow((long double)S::ex(i), cp[k]) * std::pow((long double)S::ey(i), cq[k]);
+  std::vector<long double> rhs(ne);
+  for (int k = 0; k < ne; ++k) rhs[k] = odd_df(cp[k]) * odd_df(cq[k]);
+  auto mat = [&](long double r, std::vector<long double>& A) {
+    A.assign(ne * ns, 0);
+    for (int k = 0; k < ne; ++k)
+      for (int s = 0; s < ns; ++s) A[k * ns + s] = std::pow(r, cp[k] + cq[k]) * m[k * ns + s];
+  };
+  // least-squares start at r0
+  std::vector<long double> A, N(ns * ns, 0), y(ns, 0);
+  long double r = r0;
+  mat(r, A);
+  for (int a = 0; a < ns; ++a) {
+    for (int b = 0; b < ns; ++b)
+      for (int k = 0; k < ne; ++k) N[a * ns + b] += A[k * ns + a] * A[k * ns + b];
+    for (int k = 0; k < ne; ++k) y[a] += A[k * ns + a] * rhs[k];
+  }
+  if (!solve_linear(N, y, ns)) { err = "quadrature: singular start"; return false; }
+  std::vector<long double> W = y;
+  const int n = ns + 1;
+  for (int it = 0; it < 100; ++it) {
+    std::vector<long double> J(n * n, 0), F(n, 0);
+    mat(r, A);
+    for (int k = 0; k < ne; ++k) {
+      long double s = 0, sd = 0;
+      for (int j = 0; j < ns; ++j) {
+        s += A[k * ns + j] * W[j];
+        J[k * n + j] = A[k * ns + j];
+        sd += (long double)(cp[k] + cq[k]) * std::pow(r, cp[k] + cq[k] - 1) * m[k * ns + j] * W[j];
+      }
+      J[k * n + ns] = (cp[k] + cq[k]) > 0 ? sd : 0;
+      F[k] = -(s - rhs[k]);
+    }
+    if (!solve_linear(J, F, n)) { err = "quadrature: singular Newton step"; return false; }
+    long double step = 0;
+    for (int j = 0; j < ns; ++j) { W[j] += F[j]; step = std::max(step, std::fabs(F[j])); }
+    r += F[ns];
+    step = std::max(step, std::fabs(F[ns]));
+    if (step < 1e-17L) break;
+  }
+  mat(r, A);
+  double worst = 0;
+  for (int k = 0; k < ne; ++k) {
+    long double s = 0;
+    for (int j = 0; j < ns; ++j) s += A[k * ns + j] * W[j];
+    worst = std::max(worst, (double)std::fabs(s - rhs[k]));
+  }
+  for (int j = 0; j < ns; ++j)
+    if (!(W[j] > 0)) { err = "quadrature: negative weight"; return false; }
+  if (!(worst < 1e-11)) { err = "quadrature: Newton did not converge"; return false; }
+  for (int s = 0; s < ns; ++s)
+    for (int i = S::shell_first(s); i < S::shell_first(s) + S::shell_size(s); ++i)
+      w_dir[i] = (double)W[s];
+  *r_out = (double)r;
+  return true;
+}
+
+bool lattice_of(int q, double* w, double* r, std::string& err) {
+  switch (q) {
+    case 37: return derive_quadrature<D2Q37>(9, 1.2, w, r, err);
+    case 17: return derive_quadrature<D2Q17>(7, 1.64, w, r, err);
+    case 9: return derive_quadrature<D2Q9>(5, 1.73, w, r, err);
+  }
+  err = "unknown stencil";
+  return false;
+}
+
+template <class S>
+void velocities(int* e) {
+  for (int i = 0; i < S::Q; ++i) { e[2 * i] = S::ex(i); e[2 * i + 1] = S::ey(i); }
+}
+
+template <class S>
+void mean_equilibrium(const double* w, double r, const lbm_bc_params& bp, double* out) {
+  Consts<double> c{};
+  for (int i = 0; i < S::Q; ++i) c.w[i] = w[i];
+  c.r = r;
+  c.r2 = r * r;
+  Macro<double> m;
+  m.rho = bp.rho0;
+  m.drho = bp.rho0 - 1.0;
+  m.inv_rho = 1.0 / bp.rho0;
+  m.urx = r * bp.u0x;
+  m.ury = r * bp.u0y;
+  m.u2 = bp.u0x * bp.u0x + bp.u0y * bp.u0y;
+  m.theta = bp.T0 - 1.0;
+  const EqCoef<double> k = eq_coef<S::ORDER, double>(m);
+  for (int i = 0; i < S::Q; ++i) out[i] = eq_dir<S, double, false>(i, m, k, c);
+}
+
+int halo_of(int q) { return q == 9 ? 1 : 3; }
+
+}  // namespace
+
+// --------------------------------------------------------------------------------------------
+struct lbm_ctx {
+  int q = 0;
+  lbm_precision prec = LBM_FP64;
+  lbm_bc_kind bc = LBM_BC_ZG;
+  int device = 0;
+  Geom g{};
+  OpsTable ops{};
+  Dev dev{};
+  double w[kMaxQ]{}, r = 0, tau = 0, omega = 0;
+  cudaStream_t st = nullptr;
+  void* f[2] = {nullptr, nullptr};
+  void* S[2] = {nullptr, nullptr};
+  double* V = nullptr;        // 4 arrays of [4][nb]: targets, stage a, stage b, accumulator
+  double* Uedge = nullptr;
+  double* staging = nullptr;  // [4][Lx*Ly]
+  double* partials = nullptr;
+  int max_blocks = 0;
+  double* dout = nullptr;
+  double* hout = nullptr;     // pinned
+  int* hflag = nullptr;       // mapped pinned
+  int* dflag = nullptr;
+  size_t fbytes = 0, sbytes = 0;
+  int cur = 0, scur = 0;
+  bool initialized = false, prev_valid = false, prev_prestream = false;
+  long long steps = 0;
+  std::string err;
+};
+
+#define LBM_CK(call)                                                          \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+      return LBM_ECUDA;                                                       \
+    }                                                                         \
+  } while (0)
+
+static void free_all(lbm_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->st) cudaStreamSynchronize(ctx->st); else cudaDeviceSynchronize();
+  for (int k = 0; k < 2; ++k) { cudaFree(ctx->f[k]); cudaFree(ctx->S[k]); }
+  cudaFree(ctx->V);
+  cudaFree(ctx->Uedge);
+  cudaFree(ctx->staging);
+  cudaFree(ctx->partials);
+  cudaFree(ctx->dout);
+  if (ctx->hout) cudaFreeHost(ctx->hout);
+  if (ctx->hflag) cudaFreeHost(ctx->hflag);
+}
+
+static void set_roles(lbm_ctx* ctx, int a, int s) {
+  Dev& d = ctx->dev;
+  d.A = ctx->f[a];
+  d.B = ctx->f[1 - a];
+  d.Sold = ctx->S[s];
+  d.Snew = ctx->S[1 - s];
+}
+
+static lbm_status check_ready(lbm_ctx* ctx) {
+  if (!ctx) return LBM_EINVAL;
+  if (!ctx->initialized) { ctx->err = "context not initialized"; return LBM_ESTATE; }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) { ctx->err = "cudaSetDevice failed"; return LBM_ECUDA; }
+  return LBM_OK;
+}
+
+extern "C" {
+
+lbm_status lbm_lattice_info(lbm_stencil stencil, int* q, int* e, double* w, double* r) {
+  double ww[kMaxQ], rr;
+  std::string err;
+  if (!lattice_of((int)stencil, ww, &rr, err)) { g_create_error = err; return LBM_EINVAL; }
+  const int qq = (int)stencil;
+  if (q) *q = qq;
+  if (w) std::memcpy(w, ww, sizeof(double) * qq);
+  if (r) *r = rr;
+  if (e) {
+    if (qq == 37) velocities<D2Q37>(e);
+    else if (qq == 17) velocities<D2Q17>(e);
+    else velocities<D2Q9>(e);
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int pml_width,
+                      const lbm_sigma_profile* sigma, lbm_bc_kind bc, const lbm_bc_params* bcp,
+                      lbm_precision precision, void* cuda_stream, lbm_ctx** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  auto fail = [](const char* m) { g_create_error = m; return LBM_EINVAL; };
+  if (!grid) return fail("grid is NULL");
+  const int q = (int)stencil;
+  if (q != 37 && q != 17 && q != 9) return fail("stencil must be 9, 17 or 37");
+  if (grid->nx < 8 || grid->ny < 8) return fail("bulk must be at least 8 x 8");
+  if (!(tau > 0.5)) return fail("tau must exceed 1/2");
+  if (pml_width < 0 || pml_width == 1) return fail("pml_width must be 0 or >= 2");
+  if (bc != LBM_BC_PERIODIC && bc != LBM_BC_ZG && bc != LBM_BC_NRBC) return fail("bad bc kind");
+  if (bc == LBM_BC_PERIODIC && pml_width != 0) return fail("periodic mode has no PML");
+  if (precision != LBM_FP64 && precision != LBM_FP32_DEV) return fail("bad precision");
+  lbm_sigma_profile sg = sigma ? *sigma : lbm_sigma_profile{0.0, 2};
+  if (!(sg.sigma_max >= 0.0) || !std::isfinite(sg.sigma_max) || sg.power < 0 || sg.power > 16)
+    return fail("bad sigma profile");
+  lbm_bc_params bp;
+  if (bcp) bp = *bcp;
+  else { std::memset(&bp, 0, sizeof bp); bp.rho0 = 1.0; bp.T0 = 1.0; }
+  if (!(bp.rho0 > 0) || !(bp.T0 > 0) || !std::isfinite(bp.u0x) || !std::isfinite(bp.u0y) ||
+      !std::isfinite(bp.beta))
+    return fail("bad mean state or beta");
+  for (int k = 0; k < 4; ++k)
+    if (bp.edge[k] != 0 && bp.edge[k] != 1) return fail("bad characteristic BC variant");
+  if (bp.relax_sign != 0.0 && bp.relax_sign != 1.0 && bp.relax_sign != -1.0)
+    return fail("relax_sign must be -1, +1 or 0");
+  if ((long long)grid->nx * grid->ny > (1ll << 31) / 2) return fail("grid too large");
+
+  lbm_ctx* ctx = new lbm_ctx();
+  ctx->q = q;
+  ctx->prec = precision;
+  ctx->bc = bc;
+  ctx->tau = tau;
+  ctx->omega = std::isinf(tau) ? 0.0 : 1.0 / tau;
+  ctx->st = (cudaStream_t)cuda_stream;
+  std::string lerr;
+  if (!lattice_of(q, ctx->w, &ctx->r, lerr)) { delete ctx; return fail("quadrature failed"); }
+  cudaGetDevice(&ctx->device);
+
+  Geom& g = ctx->g;
+  g.nx = grid->nx;
+  g.ny = grid->ny;
+  g.W = pml_width;
+  g.M = halo_of(q);
+  g.Lx = g.nx + 2 * g.W;
+  g.Ly = g.ny + 2 * g.W;
+  g.cF0 = 32;
+  g.pitch = ((g.cF0 + g.Lx + g.M) + 31) / 32 * 32;
+  g.plane = ((long long)g.pitch * (g.Ly + 2 * g.M) + 63) / 64 * 64;
+  g.Wf = g.W > 0 ? std::max(g.W + 1, g.M) : g.M;
+  g.frame_n = 2 * g.Wf * g.Lx + 2 * (g.Ly - 2 * g.Wf) * g.Wf;
+  g.Sp = g.W > 0 ? ((long long)g.frame_n + 31) / 32 * 32 : 0;
+  g.nb = 2 * g.M * (g.Lx + g.Ly);
+  g.ne = 4 * (g.Lx + g.Ly);
+  g.ngamma = 2 * g.M * (g.Lx + 2 * g.M) + 2 * g.M * g.Ly;
+
+  switch (q * 2 + (precision == LBM_FP32_DEV)) {
+    case 74: ctx->ops = ops_q37_f64(); break;
+    case 75: ctx->ops = ops_q37_f32(); break;
+    case 34: ctx->ops = ops_q17_f64(); break;
+    case 35: ctx->ops = ops_q17_f32(); break;
+    case 18: ctx->ops = ops_q9_f64(); break;
+    default: ctx->ops = ops_q9_f32(); break;
+  }
+  const int es = ctx->ops.elem_size;
+  ctx->fbytes = (size_t)q * g.plane * es;
+  ctx->sbytes = (size_t)q * g.Sp * es;
+  const size_t fieldbytes = (size_t)4 * g.Lx * g.Ly * sizeof(double);
+  ctx->max_blocks = ((g.Lx + 31) / 32) * ((g.Ly + 7) / 8);
+
+  auto oom = [&](const char* what) {
+    g_create_error = std::string("allocation failed: ") + what;
+    free_all(ctx);
+    delete ctx;
+    return LBM_ENOMEM;
+  };
+  for (int k = 0; k < 2; ++k) {
+    if (cudaMalloc(&ctx->f[k], ctx->fbytes) != cudaSuccess) return oom("populations");
+    if (cudaMemset(ctx->f[k], 0, ctx->fbytes) != cudaSuccess) return oom("populations");
+    if (g.W > 0) {
+      if (cudaMalloc(&ctx->S[k], ctx->sbytes) != cudaSuccess) return oom("PML accumulator");
+      if (cudaMemset(ctx->S[k], 0, ctx->sbytes) != cudaSuccess) return oom("PML accumulator");
+    }
+  }
+  if (cudaMalloc(&ctx->V, sizeof(double) * 16 * (size_t)g.nb) != cudaSuccess) return oom("targets");
+  if (cudaMalloc(&ctx->Uedge, sizeof(double) * 4 * (size_t)g.ne) != cudaSuccess) return oom("edges");
+  cudaMemset(ctx->V, 0, sizeof(double) * 16 * (size_t)g.nb);
+  cudaMemset(ctx->Uedge, 0, sizeof(double) * 4 * (size_t)g.ne);
+  if (cudaMalloc(&ctx->staging, fieldbytes) != cudaSuccess) return oom("staging");
+  if (cudaMalloc(&ctx->partials, sizeof(double) * 12 * (size_t)ctx->max_blocks) != cudaSuccess)
+    return oom("partials");
+  if (cudaMalloc(&ctx->dout, sizeof(double) * 16) != cudaSuccess) return oom("outputs");
+  if (cudaHostAlloc(&ctx->hout, sizeof(double) * 16, cudaHostAllocDefault) != cudaSuccess)
+    return oom("pinned outputs");
+  if (cudaHostAlloc(&ctx->hflag, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
+    return oom("status flag");
+  *ctx->hflag = 0;
+  if (cudaHostGetDevicePointer((void**)&ctx->dflag, ctx->hflag, 0) != cudaSuccess)
+    return oom("status flag mapping");
+
+  Dev& d = ctx->dev;
+  d.g = g;
+  d.st = ctx->st;
+  d.flag = ctx->dflag;
+  d.Vtgt = ctx->V;
+  d.Va = ctx->V + 4 * (size_t)g.nb;
+  d.Vb = ctx->V + 8 * (size_t)g.nb;
+  d.Vacc = ctx->V + 12 * (size_t)g.nb;
+  d.Uedge = ctx->Uedge;
+  d.bc.bc = (int)bc;
+  for (int k = 0; k < 4; ++k) d.bc.edge[k] = bp.edge[k];
+  d.bc.beta = bp.beta;
+  d.bc.relax_sign = bp.relax_sign == 0.0 ? -1.0 : bp.relax_sign;
+  d.bc.r = ctx->r;
+  d.bc.omega = ctx->omega;
+  double fbar[kMaxQ];
+  if (q == 37) mean_equilibrium<D2Q37>(ctx->w, ctx->r, bp, fbar);
+  else if (q == 17) mean_equilibrium<D2Q17>(ctx->w, ctx->r, bp, fbar);
+  else mean_equilibrium<D2Q9>(ctx->w, ctx->r, bp, fbar);
+  std::memset(&d.cd, 0, sizeof d.cd);
+  std::memset(&d.cf, 0, sizeof d.cf);
+  for (int i = 0; i < q; ++i) {
+    d.cd.w[i] = ctx->w[i];
+    d.cd.eqbar[i] = fbar[i];
+    d.cf.w[i] = (float)ctx->w[i];
+    d.cf.eqbar[i] = (float)(fbar[i] - ctx->w[i]);
+  }
+  d.cd.r = ctx->r; d.cd.r2 = ctx->r * ctx->r; d.cd.omega = ctx->omega;
+  d.cd.sigma_max = sg.sigma_max; d.cd.power = sg.power;
+  d.cf.r = (float)ctx->r; d.cf.r2 = (float)(ctx->r * ctx->r); d.cf.omega = (float)ctx->omega;
+  d.cf.sigma_max = (float)sg.sigma_max; d.cf.power = sg.power;
+  if (cudaDeviceSynchronize() != cudaSuccess) return oom("device sync");
+  *out = ctx;
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* ctx) {
+  if (!ctx) return LBM_OK;
+  free_all(ctx);
+  delete ctx;
+  return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+lbm_status lbm_geometry(const lbm_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) return LBM_EINVAL;
+  const Geom& g = ctx->g;
+  out[0] = g.nx; out[1] = g.ny; out[2] = g.W; out[3] = g.M;
+  out[4] = g.Lx; out[5] = g.Ly; out[6] = ctx->q; out[7] = ctx->steps;
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+// characteristic targets at initialization: the fields at the nearest fluid node x_f
+namespace lbm {
+__global__ void k_init_targets(Geom g, const double* rho, const double* ux, const double* uy,
+                               const double* T, double* V) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= g.nb) return;
+  const int M = g.M, Lx = g.Lx, Ly = g.Ly;
+  int x, y;
+  if (b < M * Ly) { y = b % Ly; x = 0; }
+  else if (b < 2 * M * Ly) { y = (b - M * Ly) % Ly; x = Lx - 1; }
+  else if (b < 2 * M * Ly + M * Lx) { x = (b - 2 * M * Ly) % Lx; y = 0; }
+  else { x = (b - 2 * M * Ly - M * Lx) % Lx; y = Ly - 1; }
+  const int k = y * Lx + x;
+  V[b] = rho[k];
+  V[g.nb + b] = ux[k];
+  V[2 * g.nb + b] = uy[k];
+  V[3 * g.nb + b] = T[k];
+}
+}  // namespace lbm
+
+extern "C" {
+
+lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                    const double* T, int fields_on_device) {
+  if (!ctx) return LBM_EINVAL;
+  if (!rho || !ux || !uy || !T) { ctx->err = "NULL field"; return LBM_EINVAL; }
+  LBM_CK(cudaSetDevice(ctx->device));
+  const Geom& g = ctx->g;
+  const size_t n = (size_t)g.Lx * g.Ly;
+  const double* src[4] = {rho, ux, uy, T};
+  if (!fields_on_device) {
+    for (int k = 0; k < 4; ++k)
+      LBM_CK(cudaMemcpyAsync(ctx->staging + k * n, src[k], n * sizeof(double),
+                             cudaMemcpyHostToDevice, ctx->st));
+    for (int k = 0; k < 4; ++k) src[k] = ctx->staging + k * n;
+  }
+  *ctx->hflag = 0;
+  Dev& d = ctx->dev;
+  set_roles(ctx, 0, 0);
+  LBM_CK(ctx->ops.init_eq(d, src[0], src[1], src[2], src[3]));
+  if (ctx->bc == LBM_BC_NRBC) {
+    k_init_targets<<<(g.nb + 127) / 128, 128, 0, ctx->st>>>(g, src[0], src[1], src[2], src[3],
+                                                            d.Vtgt);
+    LBM_CK(cudaGetLastError());
+  }
+  // initial collision (no streaming): buffer 0 holds f^0, buffer 1 receives f*^0
+  LBM_CK(ctx->ops.step(d, false));
+  LBM_CK(cudaStreamSynchronize(ctx->st));
+  ctx->cur = 1;
+  ctx->scur = 1;
+  ctx->steps = 0;
+  ctx->initialized = true;
+  ctx->prev_valid = true;
+  ctx->prev_prestream = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int n) {
+  lbm_status s = check_ready(ctx);
+  if (s != LBM_OK) return s;
+  if (n < 0) { ctx->err = "negative step count"; return LBM_EINVAL; }
+  if (*(volatile int*)ctx->hflag) { ctx->err = "unphysical state flagged"; return LBM_EUNSTABLE; }
+  for (int k = 0; k < n; ++k) {
+    set_roles(ctx, ctx->cur, ctx->scur);
+    LBM_CK(ctx->ops.step(ctx->dev, true));
+    ctx->cur ^= 1;
+    ctx->scur ^= 1;
+    ctx->steps++;
+  }
+  if (n > 0) { ctx->prev_valid = true; ctx->prev_prestream = false; }
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* ctx) {
+  if (!ctx) return LBM_EINVAL;
+  LBM_CK(cudaSetDevice(ctx->device));
+  LBM_CK(cudaStreamSynchronize(ctx->st));
+  if (*(volatile int*)ctx->hflag) { ctx->err = "unphysical state flagged"; return LBM_EUNSTABLE; }
+  return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* ux, double* uy, double* T, int region,
+                       int out_on_device) {
+  lbm_status s = check_ready(ctx);
+  if (s != LBM_OK) return s;
+  if (!ctx->prev_valid) { ctx->err = "populations were imported; step first"; return LBM_ESTATE; }
+  const Geom& g = ctx->g;
+  const size_t n = region ? (size_t)g.Lx * g.Ly : (size_t)g.nx * g.ny;
+  double* user[4] = {rho, ux, uy, T};
+  double* o[4];
+  for (int k = 0; k < 4; ++k) o[k] = out_on_device ? user[k] : (user[k] ? ctx->staging + k * n : nullptr);
+  const double* r[4] = {nullptr, nullptr, nullptr, nullptr};
+  int nblk = 0;
+  LBM_CK(ctx->ops.fields(ctx->dev, ctx->f[1 - ctx->cur], !ctx->prev_prestream, region ? 1 : 0, o,
+                         r, 1, nullptr, &nblk));
+  if (!out_on_device)
+    for (int k = 0; k < 4; ++k)
+      if (user[k])
+        LBM_CK(cudaMemcpyAsync(user[k], o[k], n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  LBM_CK(cudaStreamSynchronize(ctx->st));
+  if (*(volatile int*)ctx->hflag) { ctx->err = "unphysical state flagged"; return LBM_EUNSTABLE; }
+  return LBM_OK;
+}
+
+static lbm_status reduce_common(lbm_ctx* ctx, int mode, const double* const r[4], unsigned min_mask,
+                                double* out, int nout) {
+  double* o[4] = {nullptr, nullptr, nullptr, nullptr};
+  int nblk = 0;
+  LBM_CK(ctx->ops.fields(ctx->dev, ctx->f[1 - ctx->cur], !ctx->prev_prestream, mode == 2 ? 1 : 0,
+                         o, r, mode, ctx->partials, &nblk));
+  LBM_CK(reduce_partials(ctx->partials, nblk, min_mask, ctx->dout, ctx->st));
+  LBM_CK(cudaMemcpyAsync(ctx->hout, ctx->dout, sizeof(double) * 12, cudaMemcpyDeviceToHost, ctx->st));
+  LBM_CK(cudaStreamSynchronize(ctx->st));
+  std::memcpy(out, ctx->hout, sizeof(double) * nout);
+  return LBM_OK;
+}
+
+lbm_status lbm_reduce(lbm_ctx* ctx, double* out) {
+  lbm_status s = check_ready(ctx);
+  if (s != LBM_OK) return s;
+  if (!out) return LBM_EINVAL;
+  if (!ctx->prev_valid) { ctx->err = "populations were imported; step first"; return LBM_ESTATE; }
+  const double* r[4] = {nullptr, nullptr, nullptr, nullptr};
+  return reduce_common(ctx, 2, r, (1u << 4) | (1u << 5), out, 7);
+}
+
+lbm_status lbm_error_sums(lbm_ctx* ctx, const double* ref_rho, const double* ref_ux,
+                          const double* ref_uy, const double* ref_T, double* out) {
+  lbm_status s = check_ready(ctx);
+  if (s != LBM_OK) return s;
+  if (!out || !ref_rho || !ref_ux || !ref_uy || !ref_T) return LBM_EINVAL;
+  if (!ctx->prev_valid) { ctx->err = "populations were imported; step first"; return LBM_ESTATE; }
+  const double* r[4] = {ref_rho, ref_ux, ref_uy, ref_T};
+  return reduce_common(ctx, 4, r, 0u, out, 12);
+}
+
+lbm_status lbm_export_populations(lbm_ctx* ctx, double* host) {
+  lbm_status s = check_ready(ctx);
+  if (s != LBM_OK) return s;
+  if (!host) return LBM_EINVAL;
+  const Geom& g = ctx->g;
+  const size_t n = (size_t)ctx->q * (g.Lx + 2 * g.M) * (g.Ly + 2 * g.M);
+  double* tmp = nullptr;
+  LBM_CK(cudaMalloc(&tmp, n * sizeof(double)));
+  cudaError_t e = ctx->ops.export_pop(ctx->dev, ctx->f[ctx->cur], tmp);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  cudaFree(tmp);
+  LBM_CK(e);
+  return LBM_OK;
+}
+
+lbm_status lbm_import_populations(lbm_ctx* ctx, const double* host) {
+  lbm_status s = check_ready(ctx);
+  if (s != LBM_OK) return s;
+  if (!host) return LBM_EINVAL;
+  const Geom& g = ctx->g;
+  const size_t n = (size_t)ctx->q * (g.Lx + 2 * g.M) * (g.Ly + 2 * g.M);
+  double* tmp = nullptr;
+  LBM_CK(cudaMalloc(&tmp, n * sizeof(double)));
+  cudaError_t e = cudaMemcpyAsync(tmp, host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st);
+  if (e == cudaSuccess) e = ctx->ops.import_pop(ctx->dev, tmp, ctx->f[ctx->cur]);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  cudaFree(tmp);
+  LBM_CK(e);
+  ctx->prev_valid = false;
+  return LBM_OK;
+}
+
+// checkpoint layout: header of 8 int64, then current and previous population buffers, the PML
+// accumulator of the current level, the targets and the saved edge moments
+struct CkptHeader { int64_t magic, q, nx, ny, W, prec, steps, flags; };
+static const int64_t kMagic = 0x4c424d434b505431ll;
+
+lbm_status lbm_checkpoint_size(const lbm_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return LBM_EINVAL;
+  *bytes = sizeof(CkptHeader) + 2 * ctx->fbytes + ctx->sbytes +
+           sizeof(double) * (4 * (size_t)ctx->g.nb + 4 * (size_t)ctx->g.ne);
+  return LBM_OK;
+}
+
+lbm_status lbm_checkpoint(lbm_ctx* ctx, void* host, size_t bytes) {
+  lbm_status s = check_ready(ctx);
+  if (s != LBM_OK) return s;
+  size_t need;
+  lbm_checkpoint_size(ctx, &need);
+  if (!host || bytes < need) { ctx->err = "checkpoint buffer too small"; return LBM_EINVAL; }
+  char* p = static_cast<char*>(host);
+  CkptHeader h{kMagic, ctx->q, ctx->g.nx, ctx->g.ny, ctx->g.W, (int64_t)ctx->prec, ctx->steps,
+               (int64_t)(ctx->prev_valid ? 1 : 0) | (int64_t)(ctx->prev_prestream ? 2 : 0)};
+  std::memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  const cudaMemcpyKind k = cudaMemcpyDeviceToHost;
+  LBM_CK(cudaMemcpyAsync(p, ctx->f[ctx->cur], ctx->fbytes, k, ctx->st)); p += ctx->fbytes;
+  LBM_CK(cudaMemcpyAsync(p, ctx->f[1 - ctx->cur], ctx->fbytes, k, ctx->st)); p += ctx->fbytes;
+  if (ctx->sbytes) { LBM_CK(cudaMemcpyAsync(p, ctx->S[ctx->scur], ctx->sbytes, k, ctx->st)); p += ctx->sbytes; }
+  LBM_CK(cudaMemcpyAsync(p, ctx->V, sizeof(double) * 4 * ctx->g.nb, k, ctx->st)); p += sizeof(double) * 4 * ctx->g.nb;
+  LBM_CK(cudaMemcpyAsync(p, ctx->Uedge, sizeof(double) * 4 * ctx->g.ne, k, ctx->st));
+  LBM_CK(cudaStreamSynchronize(ctx->st));
+  return LBM_OK;
+}
+
+lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes) {
+  if (!ctx || !host) return LBM_EINVAL;
+  LBM_CK(cudaSetDevice(ctx->device));
+  size_t need;
+  lbm_checkpoint_size(ctx, &need);
+  if (bytes < need) { ctx->err = "checkpoint buffer too small"; return LBM_EINVAL; }
+  const char* p = static_cast<const char*>(host);
+  CkptHeader h;
+  std::memcpy(&h, p, sizeof h);
+  if (h.magic != kMagic || h.q != ctx->q || h.nx != ctx->g.nx || h.ny != ctx->g.ny ||
+      h.W != ctx->g.W || h.prec != (int64_t)ctx->prec) {
+    ctx->err = "checkpoint does not match this context";
+    return LBM_EINVAL;
+  }
+  p += sizeof h;
+  const cudaMemcpyKind k = cudaMemcpyHostToDevice;
+  ctx->cur = 0;
+  ctx->scur = 0;
+  LBM_CK(cudaMemcpyAsync(ctx->f[0], p, ctx->fbytes, k, ctx->st)); p += ctx->fbytes;
+  LBM_CK(cudaMemcpyAsync(ctx->f[1], p, ctx->fbytes, k, ctx->st)); p += ctx->fbytes;
+  if (ctx->sbytes) { LBM_CK(cudaMemcpyAsync(ctx->S[0], p, ctx->sbytes, k, ctx->st)); p += ctx->sbytes; }
+  LBM_CK(cudaMemcpyAsync(ctx->V, p, sizeof(double) * 4 * ctx->g.nb, k, ctx->st)); p += sizeof(double) * 4 * ctx->g.nb;
+  LBM_CK(cudaMemcpyAsync(ctx->Uedge, p, sizeof(double) * 4 * ctx->g.ne, k, ctx->st));
+  LBM_CK(cudaStreamSynchronize(ctx->st));
+  ctx->steps = h.steps;
+  ctx->prev_valid = (h.flags & 1) != 0;
+  ctx->prev_prestream = (h.flags & 2) != 0;
+  ctx->initialized = true;
+  *ctx->hflag = 0;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,527 @@
+// Device side of the PML + outer-boundary thermal lattice Boltzmann step (arXiv 2504.20169).
+//
+// Storage. Populations are SoA planes p[i][row][col] over the grid G = F + M boundary layers.
+// Node (x, y) of F (0 <= x < Lx) sits at row y + M, column cF0 + x, where cF0 is a multiple of
+// 32, so every warp-aligned run of 32 nodes of F starts on a 128 B (FP32) / 256 B (FP64)
+// boundary. In LBM_FP32_DEV storage each value is g_i = f_i - w_i (deviation from the rest
+// state), otherwise the absolute f_i in FP64.
+//
+// A stored buffer always holds post-collision populations f* of one time level; a step pulls
+// f^(n+1)(x) = f*^n(x - e_i) (Eq. lbe), collides, and writes f*^(n+1).
+//
+// Work split of one step (all kernels read buffer A and write disjoint parts of buffer B):
+//   k_nrbc_stage x4   characteristic targets U_tgt^(n+1) on the edge bands (Sec. 4)
+//   k_bulk            nodes of F at distance >= Wf from the outer edge: BGK only
+//   k_frame1          the frame (distance < Wf): BGK, PML accumulator, local PML terms,
+//                     saving the outer two layers' moments for the characteristic BC
+//   k_frame2          PML nodes: the gradient part of Omega^PML (needs the frame's new Q)
+//   k_gamma           the M boundary layers outside F (zero gradient, characteristic BC with
+//                     non-equilibrium extrapolation, or periodic images)
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "stencils.cuh"
+
+namespace lbm {
+
+constexpr int kMaxQ = 37;
+
+struct Geom {
+  int nx, ny, W, M, Lx, Ly;
+  int pitch;         // storage row length (elements), multiple of 32
+  int cF0;           // storage column of x = 0 of F, multiple of 32
+  long long plane;   // elements per direction plane (pitch * (Ly + 2M))
+  int Wf;            // frame depth: max(W + 1, M) when W > 0 or periodic, else M
+  int frame_n;       // number of frame nodes
+  long long Sp;      // PML accumulator stride per direction
+  int nb;            // characteristic-BC band nodes: 2 M (Lx + Ly)
+  int ne;            // saved fluid-moment slots: 4 (Lx + Ly) (two layers per edge)
+  int ngamma;        // boundary nodes outside F: 2M(Lx + 2M) + 2M Ly
+};
+
+// Lattice and physics constants in the arithmetic type of a kernel. eqbar holds the
+// equilibrium of the PML mean state (Eq. decomp-NJ) in the storage representation.
+template <class Real>
+struct Consts {
+  Real w[kMaxQ];
+  Real eqbar[kMaxQ];
+  Real r, r2, omega, sigma_max;
+  int power;
+};
+
+struct BcParams {
+  int bc;            // 0 periodic, 1 zero gradient, 2 characteristic
+  int edge[4];       // W E S N: 0 PNR-LODI, 1 CBC relax
+  double beta, relax_sign, r, omega;
+};
+
+__host__ __device__ inline long long gindex(const Geom& g, int x, int y) {
+  return (long long)(y + g.M) * g.pitch + g.cF0 + x;
+}
+
+__device__ inline int dist_out(const Geom& g, int x, int y) {
+  return min(min(x, g.Lx - 1 - x), min(y, g.Ly - 1 - y));
+}
+
+// Frame of depth Wf: bottom rows, top rows, then left and right columns of the middle rows.
+__device__ inline void frame_xy(const Geom& g, int fi, int& x, int& y) {
+  const int Lx = g.Lx, Wf = g.Wf;
+  const int bot = Wf * Lx;
+  if (fi < bot) { y = fi / Lx; x = fi - y * Lx; return; }
+  fi -= bot;
+  if (fi < bot) { int t = fi / Lx; y = g.Ly - Wf + t; x = fi - t * Lx; return; }
+  fi -= bot;
+  const int side = (g.Ly - 2 * Wf) * Wf;
+  if (fi < side) { int t = fi / Wf; y = Wf + t; x = fi - t * Wf; return; }
+  fi -= side;
+  int t = fi / Wf;
+  y = Wf + t;
+  x = g.Lx - Wf + (fi - t * Wf);
+}
+
+__device__ inline int frame_index(const Geom& g, int x, int y) {
+  const int Lx = g.Lx, Wf = g.Wf;
+  if (y < Wf) return y * Lx + x;
+  if (y >= g.Ly - Wf) return Wf * Lx + (y - (g.Ly - Wf)) * Lx + x;
+  const int base = 2 * Wf * Lx;
+  if (x < Wf) return base + (y - Wf) * Wf + x;
+  return base + (g.Ly - 2 * Wf) * Wf + (y - Wf) * Wf + (x - (g.Lx - Wf));
+}
+
+// sigma of Eq. (PML_ramp) at distance d (0 = outermost layer) from the edge of F.
+template <class Real>
+__device__ inline Real sigma_at(const Consts<Real>& c, int W, int d) {
+  const Real s = Real(W - d) / Real(W);
+  Real p = Real(1);
+  for (int k = 0; k < c.power; ++k) p *= s;
+  return c.sigma_max * p;
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-node arithmetic
+// ------------------------------------------------------------------------------------------
+
+// Macroscopic state of a node: rho, the velocity scaled by r (so xi_i . u = ex urx + ey ury),
+// u^2 and theta = T - 1. drho = rho - 1 is kept for the deviation storage.
+template <class Real>
+struct Macro {
+  Real rho, drho, urx, ury, u2, theta, inv_rho;
+};
+
+// Eq. (macro) on stored values p (absolute f, or g = f - w when DEV).
+template <class S, class Real, bool DEV>
+__host__ __device__ inline Macro<Real> moments(const Real (&p)[S::Q], const Consts<Real>& c) {
+  Real s0 = 0, sx = 0, sy = 0, s2 = 0;
+#pragma unroll
+  for (int i = 0; i < S::Q; ++i) {
+    s0 += p[i];
+    if (S::ex(i) != 0) sx += Real(S::ex(i)) * p[i];
+    if (S::ey(i) != 0) sy += Real(S::ey(i)) * p[i];
+    if (i != 0) s2 += Real(e2_of<S>(i)) * p[i];
+  }
+  Macro<Real> m;
+  if (DEV) {
+    m.drho = s0;
+    m.rho = Real(1) + s0;
+  } else {
+    m.rho = s0;
+    m.drho = s0 - Real(1);
+  }
+  m.inv_rho = Real(1) / m.rho;
+  // rho u = sum f xi = r sum f e (the rest weights carry no momentum)
+  const Real ux = c.r * sx * m.inv_rho, uy = c.r * sy * m.inv_rho;
+  m.urx = c.r * ux;
+  m.ury = c.r * uy;
+  m.u2 = ux * ux + uy * uy;
+  // D rho T = sum f |xi|^2 - rho u^2 with D = 2; sum w |xi|^2 = D for the deviation form
+  if (DEV)
+    m.theta = Real(0.5) * (c.r2 * s2 * m.inv_rho - m.u2 - Real(2) * m.drho * m.inv_rho);
+  else
+    m.theta = Real(0.5) * (c.r2 * s2 * m.inv_rho - m.u2) - Real(1);
+  return m;
+}
+
+// Site coefficients of the equilibrium polynomial in a = xi . u (Eqs. feq-2/3/4):
+//   P(a) = C0 + C1 a + C2 a^2 + C3 a^3 + C4 a^4,   C0 = k00 + c2 (k01 + c2 k02),
+//   C1 = k10 + c2 k11, C2 = k20 + c2 k21, C3 = 1/6 (order >= 3), C4 = 1/24 (order 4),
+// with c2 = |xi|^2 of the shell. k00m = k00 - 1 (for the deviation form, no cancellation).
+template <class Real>
+struct EqCoef {
+  Real k00m, k01, k02, k10, k11, k20, k21;
+};
+
+template <int ORDER, class Real>
+__host__ __device__ inline EqCoef<Real> eq_coef(const Macro<Real>& m) {
+  const Real u2 = m.u2, th = m.theta;
+  EqCoef<Real> k;
+  if (ORDER >= 4) {
+    k.k00m = -Real(0.5) * u2 - th + Real(0.125) * u2 * u2 + th * u2 + th * th;
+    k.k01 = Real(0.5) * th - Real(0.25) * th * u2 - th * th;
+    k.k02 = Real(0.125) * th * th;
+    k.k20 = Real(0.5) - Real(0.25) * u2 - Real(1.5) * th;
+    k.k21 = Real(0.25) * th;
+  } else {
+    k.k00m = -Real(0.5) * u2 - th;
+    k.k01 = Real(0.5) * th;
+    k.k02 = Real(0);
+    k.k20 = Real(0.5);
+    k.k21 = Real(0);
+  }
+  if (ORDER >= 3) {
+    k.k10 = Real(1) - Real(0.5) * u2 - Real(2) * th;
+    k.k11 = Real(0.5) * th;
+  } else {
+    k.k10 = Real(1);
+    k.k11 = Real(0);
+  }
+  return k;
+}
+
+// Equilibrium of direction i in the storage representation: f_eq (absolute) or
+// f_eq - w = w (rho (P - 1) + drho) (deviation).
+template <class S, class Real, bool DEV>
+__host__ __device__ inline Real eq_dir(int i, const Macro<Real>& m, const EqCoef<Real>& k,
+                              const Consts<Real>& c) {
+  const Real c2 = c.r2 * Real(e2_of<S>(i));
+  const Real a = Real(S::ex(i)) * m.urx + Real(S::ey(i)) * m.ury;
+  const Real C0m = k.k00m + c2 * (k.k01 + c2 * k.k02);
+  const Real C1 = k.k10 + c2 * k.k11;
+  const Real C2 = k.k20 + c2 * k.k21;
+  Real poly = C2;
+  if (S::ORDER >= 3) {
+    Real C34 = Real(1.0 / 6.0);
+    if (S::ORDER >= 4) C34 = C34 + a * Real(1.0 / 24.0);
+    poly = poly + a * C34;
+  }
+  const Real Pm1 = C0m + a * (C1 + a * poly);  // P - 1
+  if (DEV) return c.w[i] * (m.rho * Pm1 + m.drho);
+  return c.w[i] * m.rho * (Real(1) + Pm1);
+}
+
+// Same, for all directions at once using the +/- pairing: E(a) = C0 + a^2 (C2 + a^2 C4),
+// O(a) = a (C1 + a^2 C3), P(+-a) = E +- O. Writes out[i] = post-collision f + omega (eq - f).
+template <class S, class Real, bool DEV>
+__device__ inline void collide_bgk(Real (&p)[S::Q], const Macro<Real>& m,
+                                   const Consts<Real>& c) {
+  const EqCoef<Real> k = eq_coef<S::ORDER, Real>(m);
+  const Real om = c.omega;
+#pragma unroll
+  for (int s = 0; s < S::NSHELL; ++s) {
+    const int i0 = S::shell_first(s);
+    const int n = S::shell_size(s);
+    const Real c2 = c.r2 * Real(e2_of<S>(i0));
+    const Real C0m = k.k00m + c2 * (k.k01 + c2 * k.k02);
+    const Real C1 = k.k10 + c2 * k.k11;
+    const Real C2 = k.k20 + c2 * k.k21;
+    const Real wr = c.w[i0] * m.rho;          // w rho (all members of a shell share w)
+    const Real wd = c.w[i0] * m.drho;
+    if (n == 1) {
+      const Real eq = DEV ? (wr * C0m + wd) : (wr + wr * C0m);
+      p[i0] = p[i0] + om * (eq - p[i0]);
+      continue;
+    }
+#pragma unroll
+    for (int h = 0; h < n / 2; ++h) {
+      const int ip = i0 + h, im = i0 + h + n / 2;
+      const Real a = Real(S::ex(ip)) * m.urx + Real(S::ey(ip)) * m.ury;
+      const Real a2 = a * a;
+      Real Ev = C2;
+      if (S::ORDER >= 4) Ev = Ev + a2 * Real(1.0 / 24.0);
+      Ev = C0m + a2 * Ev;                      // E - 1
+      Real Ov = C1;
+      if (S::ORDER >= 3) Ov = Ov + a2 * Real(1.0 / 6.0);
+      Ov = a * Ov;
+      Real eqp, eqm;
+      if (DEV) {
+        const Real base = wr * Ev + wd;
+        const Real odd = wr * Ov;
+        eqp = base + odd;
+        eqm = base - odd;
+      } else {
+        const Real base = wr + wr * Ev;
+        const Real odd = wr * Ov;
+        eqp = base + odd;
+        eqm = base - odd;
+      }
+      p[ip] = p[ip] + om * (eqp - p[ip]);
+      p[im] = p[im] + om * (eqm - p[im]);
+    }
+  }
+}
+
+template <class Real>
+__device__ inline bool unphysical(const Macro<Real>& m) {
+  const Real T = Real(1) + m.theta;
+  return !(m.rho > Real(0)) || !(T > Real(0)) || !(m.rho < Real(1e30)) || !(T < Real(1e30));
+}
+
+template <class S, class Real, bool STREAM>
+__device__ inline void load_pop(Real (&p)[S::Q], const Real* __restrict__ A, const Geom& g,
+                                long long idx) {
+#pragma unroll
+  for (int i = 0; i < S::Q; ++i) {
+    const long long src = STREAM ? idx - (long long)S::ey(i) * g.pitch - S::ex(i) : idx;
+    p[i] = __ldg(A + (long long)i * g.plane + src);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Kernels
+// ------------------------------------------------------------------------------------------
+
+// Interior of F (distance >= Wf from its outer edge): pull, moments, BGK, store.
+// Block: 32 x BY threads; the x tiles start on a 32-node boundary of F.
+template <class S, class Real, bool DEV, bool STREAM>
+__global__ void __launch_bounds__(256) k_bulk(Geom g, Consts<Real> c, const Real* __restrict__ A,
+                                              Real* __restrict__ B, int* flag) {
+  const int x0 = (g.Wf / 32) * 32;
+  const int x = x0 + blockIdx.x * 32 + threadIdx.x;
+  const int y = g.Wf + blockIdx.y * blockDim.y + threadIdx.y;
+  if (x < g.Wf || x >= g.Lx - g.Wf || y >= g.Ly - g.Wf) return;
+  const long long idx = gindex(g, x, y);
+  Real p[S::Q];
+  load_pop<S, Real, STREAM>(p, A, g, idx);
+  const Macro<Real> m = moments<S, Real, DEV>(p, c);
+  if (unphysical(m)) *flag = 1;
+  collide_bgk<S, Real, DEV>(p, m, c);
+#pragma unroll
+  for (int i = 0; i < S::Q; ++i) B[(long long)i * g.plane + idx] = p[i];
+}
+
+// Writes the time-level moments of a node in the outer two layers of F into every edge slot
+// that refers to it (the characteristic BC reads them at the next step).
+template <class Real>
+__device__ inline void save_edge_moments(const Geom& g, double* Ue, int x, int y,
+                                         const Macro<Real>& m, Real r) {
+  const double rho = double(m.rho), ux = double(m.urx / r), uy = double(m.ury / r);
+  const double T = 1.0 + double(m.theta);
+  const int ne = g.ne;
+  auto put = [&](int slot) {
+    Ue[slot] = rho;
+    Ue[ne + slot] = ux;
+    Ue[2 * ne + slot] = uy;
+    Ue[3 * ne + slot] = T;
+  };
+  const int Lx = g.Lx, Ly = g.Ly;
+  // slot layout: W [2][Ly], E [2][Ly], S [2][Lx], N [2][Lx]
+  if (x < 2) put(x * Ly + y);
+  if (x >= Lx - 2) put(2 * Ly + (Lx - 1 - x) * Ly + y);
+  if (y < 2) put(4 * Ly + y * Lx + x);
+  if (y >= Ly - 2) put(4 * Ly + 2 * Lx + (Ly - 1 - y) * Lx + x);
+}
+
+// Frame, phase 1: BGK plus, on P and its inner ring, the trapezoidal accumulator
+// S = Q + f_hat / 2 (Eq. PMLQ: Q^n = S^(n-1) + f_hat^n / 2, S^n = S^(n-1) + f_hat^n), and on P
+// the local part -sigma (2 f_hat + sigma Q) of Eq. (PMLCOLL).
+template <class S, class Real, bool DEV, bool STREAM>
+__global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Real* __restrict__ A,
+                                                Real* __restrict__ B, const Real* __restrict__ Sold,
+                                                Real* __restrict__ Snew, double* Uedge, int save_edges,
+                                                int* flag) {
+  const int fi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (fi >= g.frame_n) return;
+  int x, y;
+  frame_xy(g, fi, x, y);
+  const int d = dist_out(g, x, y);
+  const long long idx = gindex(g, x, y);
+  Real p[S::Q];
+  load_pop<S, Real, STREAM>(p, A, g, idx);
+  const Macro<Real> m = moments<S, Real, DEV>(p, c);
+  if (unphysical(m)) *flag = 1;
+  if (save_edges && d < 2) save_edge_moments(g, Uedge, x, y, m, c.r);
+  const bool has_q = g.W > 0 && d <= g.W;
+  const bool in_p = g.W > 0 && d < g.W;
+  const Real sig = in_p ? sigma_at(c, g.W, d) : Real(0);
+  const EqCoef<Real> k = eq_coef<S::ORDER, Real>(m);
+#pragma unroll
+  for (int i = 0; i < S::Q; ++i) {
+    const Real eq = eq_dir<S, Real, DEV>(i, m, k, c);
+    Real out = p[i] + c.omega * (eq - p[i]);
+    if (has_q) {
+      const Real fhat = eq - c.eqbar[i];
+      const long long si = (long long)i * g.Sp + fi;
+      const Real so = Sold[si];
+      const Real q = so + Real(0.5) * fhat;
+      Snew[si] = so + fhat;
+      if (in_p) out = out - sig * (Real(2) * fhat + sig * q);
+    }
+    B[(long long)i * g.plane + idx] = out;
+  }
+}
+
+// Frame, phase 2 (PML nodes): subtract sigma e_i . grad Q_i with Q = (S^(n-1) + S^n) / 2,
+// Eq. (FD-dx-center) per axis, Eq. (FD-dx-bw) along the outward normal at the outermost layer.
+template <class S, class Real>
+__global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __restrict__ B,
+                                                const Real* __restrict__ Sold,
+                                                const Real* __restrict__ Snew) {
+  const int fi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (fi >= g.frame_n) return;
+  int x, y;
+  frame_xy(g, fi, x, y);
+  const int d = dist_out(g, x, y);
+  if (d >= g.W) return;
+  const Real sig = sigma_at(c, g.W, d);
+  // x axis: neighbours / one-sided stencil
+  int ax0, ax1, ax2;  // frame indices; derivative = cx0*Q(ax0) + cx1*Q(ax1) + cx2*Q(ax2)
+  Real cx0, cx1, cx2;
+  if (x == 0) {  // outward normal -x: dQ/dx = -(3Q(x) - 4Q(x+1) + Q(x+2))/2
+    ax0 = fi; ax1 = frame_index(g, 1, y); ax2 = frame_index(g, 2, y);
+    cx0 = Real(-1.5); cx1 = Real(2); cx2 = Real(-0.5);
+  } else if (x == g.Lx - 1) {
+    ax0 = fi; ax1 = frame_index(g, x - 1, y); ax2 = frame_index(g, x - 2, y);
+    cx0 = Real(1.5); cx1 = Real(-2); cx2 = Real(0.5);
+  } else {
+    ax0 = frame_index(g, x + 1, y); ax1 = frame_index(g, x - 1, y); ax2 = fi;
+    cx0 = Real(0.5); cx1 = Real(-0.5); cx2 = Real(0);
+  }
+  int ay0, ay1, ay2;
+  Real cy0, cy1, cy2;
+  if (y == 0) {
+    ay0 = fi; ay1 = frame_index(g, x, 1); ay2 = frame_index(g, x, 2);
+    cy0 = Real(-1.5); cy1 = Real(2); cy2 = Real(-0.5);
+  } else if (y == g.Ly - 1) {
+    ay0 = fi; ay1 = frame_index(g, x, y - 1); ay2 = frame_index(g, x, y - 2);
+    cy0 = Real(1.5); cy1 = Real(-2); cy2 = Real(0.5);
+  } else {
+    ay0 = frame_index(g, x, y + 1); ay1 = frame_index(g, x, y - 1); ay2 = fi;
+    cy0 = Real(0.5); cy1 = Real(-0.5); cy2 = Real(0);
+  }
+  const long long idx = gindex(g, x, y);
+#pragma unroll
+  for (int i = 0; i < S::Q; ++i) {
+    const Real* so = Sold + (long long)i * g.Sp;
+    const Real* sn = Snew + (long long)i * g.Sp;
+    Real gq = 0;
+    if (S::ex(i) != 0) {
+      const Real dx = cx0 * (so[ax0] + sn[ax0]) + cx1 * (so[ax1] + sn[ax1]) +
+                      cx2 * (so[ax2] + sn[ax2]);
+      gq += Real(S::ex(i)) * dx;
+    }
+    if (S::ey(i) != 0) {
+      const Real dy = cy0 * (so[ay0] + sn[ay0]) + cy1 * (so[ay1] + sn[ay1]) +
+                      cy2 * (so[ay2] + sn[ay2]);
+      gq += Real(S::ey(i)) * dy;
+    }
+    Real* b = B + (long long)i * g.plane + idx;
+    *b = *b - sig * Real(0.5) * gq;   // Q = (S^(n-1) + S^n) / 2
+  }
+}
+
+__device__ inline void gamma_xy(const Geom& g, int t, int& x, int& y) {
+  const int M = g.M, Gx = g.Lx + 2 * M;
+  if (t < M * Gx) { y = t / Gx; x = t - y * Gx - M; y -= M; return; }
+  t -= M * Gx;
+  if (t < M * Gx) { int r = t / Gx; y = g.Ly + r; x = t - r * Gx - M; return; }
+  t -= M * Gx;
+  const int r = t / (2 * M), k = t - r * 2 * M;
+  y = r;
+  x = k < M ? k - M : g.Lx + (k - M);
+}
+
+// Boundary layers outside F (Sec. 4): the post-stream populations there are set by the BC and
+// then BGK-collided (no PML term). Zero gradient (Eq. zg-bc): copy of the nearest fluid node x_f,
+// so the result equals the BGK post-collision of x_f. Characteristic BC on the edge bands:
+// f = f_eq(U_tgt) + f_neq(x_f), whose moments are U_tgt, so the collided value is
+// f_eq(U_tgt) + (1 - omega) f_neq(x_f); the corner blocks use the zero-gradient copy.
+// Periodic: the post-collision value of the periodic image.
+template <class S, class Real, bool DEV, bool STREAM>
+__global__ void __launch_bounds__(128) k_gamma(Geom g, Consts<Real> c, BcParams bc,
+                                               const Real* __restrict__ A, Real* __restrict__ B,
+                                               const double* __restrict__ Vtgt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.ngamma) return;
+  int x, y;
+  gamma_xy(g, t, x, y);
+  int sx, sy;
+  if (bc.bc == 0) {
+    sx = (x + g.Lx) % g.Lx;
+    sy = (y + g.Ly) % g.Ly;
+  } else {
+    sx = min(max(x, 0), g.Lx - 1);
+    sy = min(max(y, 0), g.Ly - 1);
+  }
+  Real p[S::Q];
+  load_pop<S, Real, STREAM>(p, A, g, gindex(g, sx, sy));
+  const Macro<Real> m = moments<S, Real, DEV>(p, c);
+  const long long dst = gindex(g, x, y);
+  const bool xo = x < 0 || x >= g.Lx, yo = y < 0 || y >= g.Ly;
+  if (bc.bc == 2 && xo != yo) {
+    // edge band node: index into the target arrays
+    int b;
+    const int M = g.M, Lx = g.Lx, Ly = g.Ly;
+    if (x < 0) b = (-x - 1) * Ly + y;
+    else if (x >= Lx) b = M * Ly + (x - Lx) * Ly + y;
+    else if (y < 0) b = 2 * M * Ly + (-y - 1) * Lx + x;
+    else b = 2 * M * Ly + M * Lx + (y - Ly) * Lx + x;
+    Macro<Real> mt;
+    const double trho = Vtgt[b], tux = Vtgt[g.nb + b], tuy = Vtgt[2 * g.nb + b],
+                 tT = Vtgt[3 * g.nb + b];
+    mt.rho = Real(trho);
+    mt.drho = Real(trho - 1.0);
+    mt.inv_rho = Real(1.0 / trho);
+    mt.urx = Real(bc.r * tux);
+    mt.ury = Real(bc.r * tuy);
+    mt.u2 = Real(tux * tux + tuy * tuy);
+    mt.theta = Real(tT - 1.0);
+    const EqCoef<Real> kf = eq_coef<S::ORDER, Real>(m);
+    const EqCoef<Real> kt = eq_coef<S::ORDER, Real>(mt);
+    const Real keep = Real(1) - c.omega;
+#pragma unroll
+    for (int i = 0; i < S::Q; ++i) {
+      const Real neq = p[i] - eq_dir<S, Real, DEV>(i, m, kf, c);
+      B[(long long)i * g.plane + dst] = eq_dir<S, Real, DEV>(i, mt, kt, c) + keep * neq;
+    }
+    return;
+  }
+  collide_bgk<S, Real, DEV>(p, m, c);
+#pragma unroll
+  for (int i = 0; i < S::Q; ++i) B[(long long)i * g.plane + dst] = p[i];
+}
+
+// ------------------------------------------------------------------------------------------
+// Characteristic targets (Sec. 4): one Runge-Kutta stage for every edge-band node.
+// ------------------------------------------------------------------------------------------
+struct Prim { double rho, un, ut, T; };
+
+// Inverse of the characteristic map: given w = S dU (acoustic-, entropy, shear, acoustic+),
+// return dU = S^-1 w in (rho, u_n, u_t, T). With P = rho T (c_s = 1), c^2 = 2 T (gamma = 2):
+// dP = (w1 + w4)/2, du_n = (w4 - w1)/(2 rho c), du_t = w3, drho = (dP + w2)/c^2,
+// dT = (dP - T drho)/rho.
+__device__ inline Prim char_inverse(const Prim& U, double c, const double w[4]) {
+  Prim d;
+  const double dP = 0.5 * (w[0] + w[3]);
+  d.un = (w[3] - w[0]) / (2.0 * U.rho * c);
+  d.ut = w[2];
+  d.rho = (dP + w[1]) / (c * c);
+  d.T = (dP - U.T * d.rho) / U.rho;
+  return d;
+}
+
+// w = S dU for the normal axis: w1 = T drho - rho c du_n + rho dT, w2 = T drho - rho dT,
+// w3 = du_t, w4 = T drho + rho c du_n + rho dT (left eigenvectors of the Euler Jacobian).
+__device__ inline void char_forward(const Prim& U, double c, const Prim& dU, double w[4]) {
+  const double dP = U.T * dU.rho + U.rho * dU.T;
+  w[0] = dP - U.rho * c * dU.un;
+  w[1] = U.T * dU.rho - U.rho * dU.T;
+  w[2] = dU.ut;
+  w[3] = dP + U.rho * c * dU.un;
+}
+
+__device__ inline Prim load_prim(const double* V, int stride, int slot, bool xaxis) {
+  Prim u;
+  u.rho = V[slot];
+  const double ux = V[stride + slot], uy = V[2 * stride + slot];
+  u.un = xaxis ? ux : uy;
+  u.ut = xaxis ? uy : ux;
+  u.T = V[3 * stride + slot];
+  return u;
+}
+
+// stage 1..4 of classical RK4 over one time step; fluid moments Ue frozen at time n.
+__global__ void k_nrbc_stage(Geom g, BcParams bc, const double* __restrict__ Ue,
+                             double* __restrict__ V0, const double* __restrict__ Vin,
+                             double* __restrict__ Vout, double* __restrict__ acc, int stage);
+
+}  // namespace lbm

@@ -1,0 +1,50 @@
+// Host-side plumbing shared by the translation units of liblbm (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Everything a launch needs: geometry, constants, the current buffer roles, the stream.
+struct Dev {
+  Geom g;
+  BcParams bc;
+  Consts<double> cd;
+  Consts<float> cf;
+  const void* A;     // post-collision populations of the current level (read)
+  void* B;           // next level (written)
+  const void* Sold;  // PML accumulator S^(n-1)
+  void* Snew;        // S^n
+  double* Vtgt;      // characteristic targets U_tgt [4][nb]
+  double* Va;        // Runge-Kutta stage buffers [4][nb]
+  double* Vb;
+  double* Vacc;
+  double* Uedge;     // fluid moments of the outer two layers of F [4][ne]
+  int* flag;         // device-visible address of the mapped "unphysical state" flag
+  cudaStream_t st;
+};
+
+struct OpsTable {
+  cudaError_t (*step)(const Dev&, bool stream);
+  cudaError_t (*init_eq)(const Dev&, const double*, const double*, const double*, const double*);
+  cudaError_t (*fields)(const Dev&, const void* src, bool stream, int region, double* const o[4],
+                        const double* const r[4], int mode, double* partials, int* nblocks);
+  cudaError_t (*export_pop)(const Dev&, const void* src, double* out);
+  cudaError_t (*import_pop)(const Dev&, const double* in, void* dst);
+  int elem_size;
+};
+
+OpsTable ops_q37_f64();
+OpsTable ops_q37_f32();
+OpsTable ops_q17_f64();
+OpsTable ops_q17_f32();
+OpsTable ops_q9_f64();
+OpsTable ops_q9_f32();
+
+// Final pass of the deterministic two-pass FP64 reduction: n partial rows of 12 values ->
+// out[12] (slots in min_mask take the minimum).
+cudaError_t reduce_partials(const double* partials, int n, unsigned min_mask, double* out,
+                            cudaStream_t st);
+
+}  // namespace lbm

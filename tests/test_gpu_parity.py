@@ -1,0 +1,166 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Tolerances over F: relative L2 of rho and T, and L2 of u_x, u_y relative to
+max(||u_ref||, c_s sqrt(N)), below 1e-12 for the FP64 path and 1e-5 for the FP32-deviation
+path; index and streaming maps bit-exact.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from parity_helpers import case_kwargs, field_errors, make_solver, rel_l2, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32dev": 1e-5}
+
+
+def check(kw, fields, steps, precision="fp64", pert_tol=None):
+    ora, _ = run_oracle(kw, fields, steps)
+    gpu = run_gpu(kw, fields, steps, precision)
+    full, pert = field_errors(gpu, ora)
+    print(f"{precision} full={['%.2e' % e for e in full]} pert={['%.2e' % e for e in pert]}")
+    assert max(full) < TOL[precision], full
+    if pert_tol is not None:
+        assert max(pert) < pert_tol, pert
+    return full, pert
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+def test_free_streaming_is_an_exact_permutation(precision):
+    """tau = inf (omega = 0): n steps move every stored population by n e_i on the periodic
+    grid, bit for bit (checks the pull index map and the periodic images)."""
+    nx, ny, n = 45, 38, 7
+    kw = case_kwargs(nx=nx, ny=ny, W=0, tau=float("inf"), bc="periodic", sigma_max=0.0)
+    with make_solver(kw, precision) as s:
+        s.init(*wl.uniform(nx, ny, 0))
+        M = s.M
+        rng = np.random.default_rng(0)
+        F = 1.0 + rng.integers(0, 1000, size=(37, ny, nx)).astype(np.float64) / 64.0
+        G = np.zeros((37, ny + 2 * M, nx + 2 * M))
+        yy = (np.arange(ny + 2 * M) - M) % ny
+        xx = (np.arange(nx + 2 * M) - M) % nx
+        G[:] = F[:, yy[:, None], xx[None, :]]
+        s.import_populations(G)
+        X0 = s.export_populations()[:, M:M + ny, M:M + nx]
+        s.step(n)
+        X = s.export_populations()[:, M:M + ny, M:M + nx]
+    from paper_2504_20169_gb300 import lattice_info
+    e, _, _ = lattice_info(37)
+    for i, (ex, ey) in enumerate(e.tolist()):
+        assert np.array_equal(X[i], np.roll(X0[i], shift=(n * ey, n * ex), axis=(0, 1))), i
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+def test_initial_fields_round_trip(precision):
+    kw = case_kwargs(nx=40, ny=36, W=5)
+    fields = wl.random_smooth_state(40, 36, 5, seed=3, du=0.1, mean_u=(0.1, 0.0))
+    with make_solver(kw, precision) as s:
+        s.init(*fields)
+        got = s.moments()
+    tol = 1e-14 if precision == "fp64" else 2e-7
+    for g, f in zip(got, fields):
+        assert np.max(np.abs(g - f)) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+def test_parity_pulse_64_pml8_zg(precision):
+    """The 64^2 + PML 8 zero-gradient pulse case (tau 0.8, cubic sigma 0.1), 200 steps."""
+    c = wl.pulse_64()
+    kw = case_kwargs(nx=c.nx, ny=c.ny, W=c.W, tau=c.tau, sigma_max=c.sigma_max,
+                     sigma_power=c.sigma_power, bc=c.bc)
+    check(kw, c.fields(), c.steps, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+def test_parity_vortex_nrbc_pml(precision):
+    """Convected isentropic vortex, NRBC (east CBC relax, others PNR-LODI) beyond a PML."""
+    kw = case_kwargs(nx=48, ny=44, W=6, tau=0.6, sigma_max=0.05, sigma_power=3, bc="nrbc",
+                     nrbc_edges=(0, 1, 0, 0), beta=0.3, mean=(1.0, 0.3, 0.0, 1.0))
+    fields = wl.isentropic_vortex(48, 44, 6, R=8.0, Mv=0.05, mean_u=(0.3, 0.0))
+    check(kw, fields, 60, precision)
+
+
+@pytest.mark.parametrize("edges", [(1, 1, 1, 1), (0, 0, 0, 0)])
+def test_parity_nrbc_without_pml(edges):
+    kw = case_kwargs(nx=40, ny=40, W=0, tau=0.7, sigma_max=0.0, bc="nrbc", nrbc_edges=edges,
+                     beta=0.2, mean=(1.0, 0.1, -0.05, 1.0))
+    fields = wl.pressure_pulse(40, 40, 0, amp=2e-3, halfwidth=4.0, u0=(0.1, -0.05))
+    check(kw, fields, 80)
+
+
+def test_parity_periodic_ragged():
+    kw = case_kwargs(nx=50, ny=38, W=0, tau=0.6, sigma_max=0.0, bc="periodic")
+    fields = wl.random_smooth_state(50, 38, 0, seed=11, du=0.1, mean_u=(0.05, 0.02))
+    check(kw, fields, 100)
+
+
+@pytest.mark.parametrize("nx,ny,W", [(45, 37, 5), (33, 70, 2), (96, 40, 35)])
+def test_parity_ragged_pml_sizes(nx, ny, W):
+    kw = case_kwargs(nx=nx, ny=ny, W=W, tau=0.75, sigma_max=0.2, sigma_power=2, bc="zg")
+    fields = wl.random_smooth_state(nx, ny, W, seed=nx + ny, du=0.05)
+    check(kw, fields, 30)
+
+
+@pytest.mark.parametrize("q", [17, 9])
+@pytest.mark.parametrize("bc", ["zg", "nrbc"])
+def test_parity_other_stencils(q, bc):
+    kw = case_kwargs(nx=36, ny=30, W=4, tau=0.7, sigma_max=0.1, bc=bc, q=q,
+                     nrbc_edges=(0, 1, 0, 1), beta=0.2, mean=(1.0, 0.05, 0.0, 1.0))
+    fields = wl.pressure_pulse(36, 30, 4, amp=1e-3, halfwidth=3.0, u0=(0.05, 0.0))
+    check(kw, fields, 50)
+
+
+def test_totals_and_error_sums_match_oracle():
+    import torch
+    kw = case_kwargs(nx=40, ny=40, W=0, tau=0.7, sigma_max=0.0, bc="periodic")
+    fields = wl.random_smooth_state(40, 40, 0, seed=5, du=0.1)
+    ora_fields, o = run_oracle(kw, fields, 25)
+    with make_solver(kw) as s:
+        s.init(*fields)
+        tot0 = s.reduce()
+        s.step(25)
+        tot = s.reduce()
+        ref = [torch.tensor(f, device="cuda") for f in ora_fields]
+        sums = s.error_sums(ref)
+        gpu_fields = s.moments(region="bulk")
+    assert np.allclose(tot[:4], o.totals(), rtol=1e-13, atol=1e-12)
+    assert np.allclose(tot[:4], tot0[:4], rtol=1e-13, atol=1e-12)   # conservation
+    assert tot[6] == 0
+    assert tot[4] == pytest.approx(ora_fields[0].min(), rel=1e-13)
+    for k, (g, r) in enumerate(zip(gpu_fields, ora_fields)):
+        assert sums[3 * k] == pytest.approx(np.sum((g - r) ** 2), rel=1e-6, abs=1e-30)
+        assert sums[3 * k + 1] == pytest.approx(np.sum(r * r), rel=1e-13)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+def test_checkpoint_restore_continues_bit_identically(precision):
+    kw = case_kwargs(nx=40, ny=36, W=6, tau=0.7, sigma_max=0.1, bc="nrbc",
+                     nrbc_edges=(1, 0, 0, 1), beta=0.3, mean=(1.0, 0.1, 0.0, 1.0))
+    fields = wl.isentropic_vortex(40, 36, 6, R=6.0, mean_u=(0.1, 0.0))
+    with make_solver(kw, precision) as a, make_solver(kw, precision) as b:
+        a.init(*fields)
+        a.step(10)
+        blob = a.checkpoint()
+        a.step(15)
+        ra = a.moments()
+        b.restore(blob)
+        b.step(15)
+        rb = b.moments()
+        assert b.steps == 25
+    for x, y in zip(ra, rb):
+        assert np.array_equal(x, y)
+
+
+def test_unphysical_state_is_reported():
+    from paper_2504_20169_gb300 import LBMError
+    kw = case_kwargs(nx=32, ny=32, W=0, bc="periodic", sigma_max=0.0)
+    with make_solver(kw) as s:
+        s.init(*wl.uniform(32, 32, 0))
+        P = s.export_populations()
+        P[:, 10, 10] = np.nan
+        s.import_populations(P)
+        s.step(1)
+        with pytest.raises(LBMError) as ei:
+            s.sync()
+        assert "UNSTABLE" in str(ei.value)
