@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Throughput of the fused PML + characteristic-BC lattice Boltzmann step on GB300.
+
+Workload (one step = one pass of the whole hot path over the grid): 2048^2 bulk + 32-node PML
+(cubic sigma, sigma_max 0.1) + characteristic outer BC (east CBC relax with beta 0.3, the other
+edges PNR-LODI), D2Q37, tau 0.55, isentropic vortex (R 20, Mach 0.05) in a Mach 0.3 mean flow.
+Synthetic seeded inputs; populations resident in HBM (1.33 GB FP32 / 2.65 GB FP64 working set,
+larger than the 129 MB L2, so no flush between steps).
+
+value   = million fluid-node updates per second (MLUPS, F = (2048 + 64)^2 nodes per step), summed
+          over ranks, FP32-deviation storage (the throughput path), device time from CUDA events
+          on the launching stream, max over ranks.
+e2e     = the same metric through the C ABI with host buffers: lbm_init from pinned host fields,
+          K steps, lbm_moments back to host, wall-clock.
+Multi-GPU: every rank runs an independent replica (instances do not exchange data), so
+scaling is weak and there is no data-path collective.
+
+--impl reference times the CPU oracle (numpy, FP64) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "vortex2048_w32_nrbc_d2q37"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="CPU-baseline budget of the oracle sample (0 skips it)")
+    ap.add_argument("--window", type=int, default=200,
+                    help="steps per fresh solve; the printed PML stays finite on this workload "
+                         "for about 300 steps (tau 0.55), so timed steps run in windows")
+    ap.add_argument("--size", type=int, default=2048,
+                    help="bulk edge (2048 = the workload; smaller sizes for profiler captures)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("lbm_device.cuh", "ops.cuh", "stencils.cuh"):
+        with open(os.path.join(ROOT, "paper_2504_20169_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip().strip("-* ")] = v.strip()
+        if kv.get("kernel_source_sha256") != kernel_source_sha():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.rows, self.proc = [], None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        if not sm:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows if len(r) > 8 for n, v in zip(names, r[5:9])
+                          if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(self.rows[0][2]),
+                "samples": len(sm), "reasons": reasons}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(seconds, n_bulk=512, steps=None):
+    """The oracle as it stands on a bounded sample of the workload: the same physics and BC mix
+    on an n_bulk^2 bulk (PML 32), stepped `steps` times or until about `seconds` have passed."""
+    import workloads as wl
+    from oracle import OracleLBM
+    c = wl.vortex_2048(n=n_bulk, W=32)
+    o = OracleLBM(c.nx, c.ny, c.W, c.tau, c.sigma_max, c.sigma_power, c.bc,
+                  nrbc_edges=c.nrbc_edges, beta=c.beta, mean=c.mean)
+    o.init(*c.fields())
+    t0 = time.perf_counter()
+    n = 0
+    while (n < steps) if steps is not None else (n < 2 or time.perf_counter() - t0 < seconds):
+        o.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    sites = (c.nx + 2 * c.W) * (c.ny + 2 * c.W)
+    return {"value": sites * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"numpy FP64 oracle, {n_bulk}^2 bulk + PML 32, same BC/physics, {n} steps, "
+                      f"{dt:.1f} s, single thread"}
+
+
+def run_reference(args, ws, rank):
+    """The oracle as the reference arm: warmup + K steps, each one oracle step on a 128^2-bulk
+    sample of the workload (PML 32, same BC and physics), so K = 300 ends in a few minutes."""
+    if rank != 0:
+        return
+    oracle_sample(0, n_bulk=128, steps=max(1, args.warmup))
+    base = oracle_sample(0, n_bulk=128, steps=max(1, args.steps))
+    line = {"metric": "MLUPS", "value": base["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": {"workload": WORKLOAD, "sample": base["sample"]},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def timed_run(Solver, c, fields, precision, steps, warmup, dev, window, prof_steps=0):
+    """Headline region: `steps` steps as repeated fresh solves of at most `window` steps (the
+    state is re-initialized, untimed, between windows), each step a CUDA-graph replay with one
+    event pair on the launching stream. Then a profiled window launched directly with CUDA
+    events around every kernel class (the interior kernel's live duration)."""
+    import torch
+    s = Solver(c.nx, c.ny, c.W, c.tau, c.sigma_max, c.sigma_power, c.bc, 37, c.nrbc_edges,
+               c.beta, c.mean, precision=precision)
+    s.init(*fields)
+    s.step(warmup)
+    s.sync()
+    st = torch.cuda.current_stream()
+    per, total, done = [], 0.0, 0
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    time.sleep(0.3)
+    while done < steps:
+        n = min(window, steps - done)
+        s.init(*fields)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+        ev[0].record(st)
+        for k in range(n):
+            s.step(1)
+            ev[k + 1].record(st)
+        torch.cuda.synchronize()
+        per += [ev[k].elapsed_time(ev[k + 1]) for k in range(n)]
+        total += ev[0].elapsed_time(ev[n])
+        done += n
+    ck = clocks.stop()
+    prof = None
+    if prof_steps:
+        s.init(*fields)
+        s.profile_enable(prof_steps)
+        s.step(prof_steps)
+        prof = s.profile_read()
+    tot = s.reduce()
+    s.close()
+    return total, per, prof, ck, tot
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_2504_20169_gb300 import Solver
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    c = wl.vortex_2048(n=args.size)
+    fields = c.fields()
+    Lx = c.nx + 2 * c.W
+    sites = Lx * Lx
+    Wf = c.W + 1
+    interior = (Lx - 2 * Wf) ** 2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    total, per, prof, ck, tot = timed_run(Solver, c, fields, "fp32dev", args.steps, args.warmup,
+                                          local, args.window,
+                                          prof_steps=min(args.steps, args.window))
+    barrier()
+    t_max = total
+    if dist is not None:
+        t = torch.tensor([total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_step = t_max / args.steps
+    value = ws * sites / (ms_step * 1e-3) / 1e6
+
+    # dominant kernel: the interior BGK kernel (D2Q37 FP32: 37 loads + 37 stores of 4 B)
+    peaks, peak_kind = measured_peaks()
+    interior_ms = prof[0]["interior"] / max(1, prof[1])
+    alg_bytes = interior * 2 * 37 * 4
+    achieved = alg_bytes / (interior_ms * 1e-3) / 1e9
+    traffic = profiled_traffic("k_bulk_fp32_vortex2048.md")
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+            "traffic": traffic, "kernel": "k_bulk<D2Q37,float,dev>",
+            "alg_bytes_per_launch": alg_bytes, "peak_source": peak_kind,
+            "kernel_ms": round(interior_ms, 4),
+            "kernel_share": {k: round(v / max(1e-9, sum(prof[0].values())), 4)
+                             for k, v in prof[0].items()}}
+    step_bytes = sites * 2 * 37 * 4
+    fp64 = None
+    if not args.no_fp64:
+        k64 = max(20, args.steps // 8)
+        total64, per64, prof64, ck64, _ = timed_run(Solver, c, fields, "fp64", k64,
+                                                     args.warmup, local, args.window,
+                                                     prof_steps=min(k64, 100))
+        ms64 = total64 / k64
+        int64_ms = prof64[0]["interior"] / max(1, prof64[1])
+        fp64 = {"value": round(sites / (ms64 * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                "ms_per_step": round(ms64, 4), "steps": k64,
+                "interior_kernel_gbs": round(interior * 2 * 37 * 8 / (int64_ms * 1e-3) / 1e9, 1),
+                "hbm_frac": round(interior * 2 * 37 * 8 / (int64_ms * 1e-3) / 1e9 /
+                                  peaks["hbm_gbs"], 4),
+                "bound": "alu (FP64 pipe)"}
+
+    # end to end through the C ABI with host buffers
+    pin = [torch.from_numpy(np.ascontiguousarray(f)).pin_memory() for f in fields]
+    outs = [torch.empty((Lx, Lx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    s = Solver(c.nx, c.ny, c.W, c.tau, c.sigma_max, c.sigma_power, c.bc, 37, c.nrbc_edges,
+               c.beta, c.mean, precision="fp32dev")
+    import ctypes as C
+    from paper_2504_20169_gb300 import _lib as L
+    barrier()
+    nrep = max(1, args.steps // args.window)
+    t0 = time.perf_counter()
+    for _ in range(nrep):
+        st = L.lib().lbm_init(s.ctx, *[C.c_void_p(p.data_ptr()) for p in pin], 0)
+        assert st == 0
+        s.step(args.window)
+        st = L.lib().lbm_moments(s.ctx, *[C.c_void_p(o.data_ptr()) for o in outs], 1, 0)
+        assert st == 0
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    s.close()
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    field_bytes = 4 * sites * 8
+    e2e = {"value": round(ws * sites * nrep * args.window / e2e_s / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": field_bytes / args.window,
+           "d2h_bytes_per_step": field_bytes / args.window,
+           "what": f"{nrep} solves through the C ABI: lbm_init from pinned host fields, "
+                   f"{args.window} steps, lbm_moments to pinned host; wall clock"}
+
+    if rank == 0:
+        cpu = oracle_sample(args.cpu_seconds) if args.cpu_seconds > 0 else None
+        per_sorted = sorted(per)
+        line = {
+            "metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.size == 2048 else f"vortex{args.size}_w32_nrbc_d2q37",
+                       "bulk": [c.nx, c.ny], "pml_width": c.W,
+                       "sigma": "cubic, sigma_max 0.1", "bc": "E: CBC relax beta 0.3; W,S,N: PNR-LODI",
+                       "tau": c.tau, "stencil": "D2Q37", "storage": "FP32 deviation from rest weights",
+                       "fluid_nodes_per_step": sites, "working_set_bytes": step_bytes,
+                       "l2": "working set 1.33 GB > 129 MB L2; no flush", "parallelism":
+                       f"replicas x{ws}"},
+            "latency_ms": {"p50": round(statistics.median(per), 5),
+                           "p99": round(per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)], 5)},
+            "roofline": roof, "fp64": fp64, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": args.steps * (8 if c.W > 0 else 7), "clocks": ck,
+            "timing": f"headline: fresh solves of {args.window} steps (untimed re-init between), "
+                      "CUDA-graph replay, events per step on the launching stream; roofline: "
+                      "interior kernel events in a separate directly launched window",
+            "totals_check": {"mass": float(tot[0]), "bad_nodes": float(tot[6])},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

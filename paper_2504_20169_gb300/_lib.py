@@ -55,6 +55,8 @@ PROTOTYPES = {
     "lbm_checkpoint_size": (C.c_int, [_ctx, C.POINTER(C.c_size_t)]),
     "lbm_checkpoint": (C.c_int, [_ctx, C.c_void_p, C.c_size_t]),
     "lbm_restore": (C.c_int, [_ctx, C.c_void_p, C.c_size_t]),
+    "lbm_profile_enable": (C.c_int, [_ctx, C.c_int]),
+    "lbm_profile_read": (C.c_int, [_ctx, _dp, C.POINTER(C.c_int)]),
     "lbm_last_error": (C.c_char_p, [_ctx]),
     "lbm_destroy": (C.c_int, [_ctx]),
 }

@@ -187,6 +187,12 @@ struct lbm_ctx {
   int cur = 0, scur = 0;
   bool initialized = false, prev_valid = false, prev_prestream = false;
   long long steps = 0;
+  cudaStream_t aux = nullptr, cap = nullptr;   // boundary-chain stream, capture stream
+  cudaEvent_t fork = nullptr, join = nullptr, ready = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one step, keyed by the buffer parity
+  bool use_graphs = true;
+  std::vector<cudaEvent_t> prof;   // kKernelClasses * 2 events per recorded step
+  int prof_cap = 0, prof_used = 0;
   std::string err;
 };
 
@@ -203,6 +209,15 @@ static void free_all(lbm_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->st) cudaStreamSynchronize(ctx->st); else cudaDeviceSynchronize();
+  for (cudaEvent_t e : ctx->prof) cudaEventDestroy(e);
+  ctx->prof.clear();
+  for (int k = 0; k < 2; ++k)
+    if (ctx->graph[k]) cudaGraphExecDestroy(ctx->graph[k]);
+  if (ctx->aux) cudaStreamDestroy(ctx->aux);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  if (ctx->join) cudaEventDestroy(ctx->join);
+  if (ctx->ready) cudaEventDestroy(ctx->ready);
   for (int k = 0; k < 2; ++k) { cudaFree(ctx->f[k]); cudaFree(ctx->S[k]); }
   cudaFree(ctx->V);
   cudaFree(ctx->Uedge);
@@ -348,9 +363,18 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   if (cudaHostGetDevicePointer((void**)&ctx->dflag, ctx->hflag, 0) != cudaSuccess)
     return oom("status flag mapping");
 
+  if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ready, cudaEventDisableTiming) != cudaSuccess)
+    return oom("streams and events");
   Dev& d = ctx->dev;
   d.g = g;
   d.st = ctx->st;
+  d.aux = ctx->aux;
+  d.fork = ctx->fork;
+  d.join = ctx->join;
   d.flag = ctx->dflag;
   d.Vtgt = ctx->V;
   d.Va = ctx->V + 4 * (size_t)g.nb;
@@ -462,14 +486,45 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const dou
   return LBM_OK;
 }
 
+// Captures one step for the current buffer parity into an executable graph (on the internal
+// capture stream; the boundary chain forks onto aux inside the capture).
+static lbm_status build_graph(lbm_ctx* ctx, int parity) {
+  set_roles(ctx, parity, parity);
+  Dev d = ctx->dev;
+  d.st = ctx->cap;
+  d.ev = nullptr;
+  LBM_CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = ctx->ops.step(d, true);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &graph);
+  LBM_CK(e);
+  LBM_CK(e2);
+  e = cudaGraphInstantiate(&ctx->graph[parity], graph, 0);
+  cudaGraphDestroy(graph);
+  LBM_CK(e);
+  return LBM_OK;
+}
+
 lbm_status lbm_step(lbm_ctx* ctx, int n) {
   lbm_status s = check_ready(ctx);
   if (s != LBM_OK) return s;
   if (n < 0) { ctx->err = "negative step count"; return LBM_EINVAL; }
   if (*(volatile int*)ctx->hflag) { ctx->err = "unphysical state flagged"; return LBM_EUNSTABLE; }
   for (int k = 0; k < n; ++k) {
-    set_roles(ctx, ctx->cur, ctx->scur);
-    LBM_CK(ctx->ops.step(ctx->dev, true));
+    const bool profiled = ctx->prof_used < ctx->prof_cap;
+    if (ctx->use_graphs && !profiled) {
+      if (!ctx->graph[ctx->cur]) {
+        lbm_status gs = build_graph(ctx, ctx->cur);
+        if (gs != LBM_OK) return gs;
+      }
+      LBM_CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->st));
+    } else {
+      set_roles(ctx, ctx->cur, ctx->scur);
+      ctx->dev.ev = nullptr;
+      if (profiled) ctx->dev.ev = &ctx->prof[(size_t)2 * kKernelClasses * ctx->prof_used++];
+      LBM_CK(ctx->ops.step(ctx->dev, true));
+      ctx->dev.ev = nullptr;
+    }
     ctx->cur ^= 1;
     ctx->scur ^= 1;
     ctx->steps++;
@@ -571,6 +626,36 @@ lbm_status lbm_import_populations(lbm_ctx* ctx, const double* host) {
   cudaFree(tmp);
   LBM_CK(e);
   ctx->prev_valid = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_enable(lbm_ctx* ctx, int max_steps) {
+  if (!ctx || max_steps < 0) return LBM_EINVAL;
+  LBM_CK(cudaSetDevice(ctx->device));
+  LBM_CK(cudaStreamSynchronize(ctx->st));
+  for (cudaEvent_t e : ctx->prof) cudaEventDestroy(e);
+  ctx->prof.clear();
+  ctx->prof_cap = ctx->prof_used = 0;
+  ctx->prof.resize((size_t)2 * kKernelClasses * max_steps);
+  for (auto& e : ctx->prof) LBM_CK(cudaEventCreate(&e));
+  ctx->prof_cap = max_steps;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_ctx* ctx, double* ms, int* steps) {
+  if (!ctx || !ms) return LBM_EINVAL;
+  LBM_CK(cudaSetDevice(ctx->device));
+  LBM_CK(cudaStreamSynchronize(ctx->st));
+  for (int k = 0; k < kKernelClasses; ++k) ms[k] = 0.0;
+  for (int s = 0; s < ctx->prof_used; ++s)
+    for (int k = 0; k < kKernelClasses; ++k) {
+      float t = 0.f;
+      LBM_CK(cudaEventElapsedTime(&t, ctx->prof[(size_t)2 * kKernelClasses * s + 2 * k],
+                                  ctx->prof[(size_t)2 * kKernelClasses * s + 2 * k + 1]));
+      ms[k] += t;
+    }
+  if (steps) *steps = ctx->prof_used;
+  ctx->prof_used = 0;
   return LBM_OK;
 }
 

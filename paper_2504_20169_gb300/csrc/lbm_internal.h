@@ -23,7 +23,16 @@ struct Dev {
   double* Uedge;     // fluid moments of the outer two layers of F [4][ne]
   int* flag;         // device-visible address of the mapped "unphysical state" flag
   cudaStream_t st;
+  // Boundary-side work (characteristic targets, frame phases, boundary band) runs on aux,
+  // forked from and joined back into st, concurrently with the interior kernel on st.
+  cudaStream_t aux;
+  cudaEvent_t fork, join;
+  // optional timing: when ev is set, event 2k / 2k+1 are recorded around kernel class k
+  // (0 characteristic targets, 1 interior, 2 frame phase 1, 3 frame phase 2, 4 boundary band)
+  cudaEvent_t* ev;
 };
+
+constexpr int kKernelClasses = 5;
 
 struct OpsTable {
   cudaError_t (*step)(const Dev&, bool stream);

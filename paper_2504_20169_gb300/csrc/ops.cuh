@@ -178,29 +178,52 @@ struct Ops {
     const Consts<Real>& c = consts(d);
     const Real* A = static_cast<const Real*>(d.A);
     Real* B = static_cast<Real*>(d.B);
+    // boundary chain on bs, interior on d.st; both read A and write disjoint parts of B
+    const cudaStream_t bs = d.aux ? d.aux : d.st;
+    auto mark = [&](int k, cudaStream_t s) {
+      if (d.ev) cudaEventRecord(d.ev[k], s);
+    };
+    if (d.aux) {
+      cudaEventRecord(d.fork, d.st);
+      cudaStreamWaitEvent(d.aux, d.fork, 0);
+    }
+    mark(0, bs);
     if (STREAM && d.bc.bc == 2) {
       const int nbk = (g.nb + 127) / 128;
       const double* Vin[4] = {d.Vtgt, d.Va, d.Vb, d.Va};
       double* Vout[4] = {d.Va, d.Vb, d.Va, nullptr};
       for (int s = 1; s <= 4; ++s)
-        k_nrbc_stage<<<nbk, 128, 0, d.st>>>(g, d.bc, d.Uedge, d.Vtgt, Vin[s - 1], Vout[s - 1],
-                                            d.Vacc, s);
+        k_nrbc_stage<<<nbk, 128, 0, bs>>>(g, d.bc, d.Uedge, d.Vtgt, Vin[s - 1], Vout[s - 1],
+                                          d.Vacc, s);
     }
+    mark(1, bs);
+    mark(4, bs);
+    k_frame1<S, Real, DEV, STREAM><<<(g.frame_n + 127) / 128, 128, 0, bs>>>(
+        g, c, A, B, static_cast<const Real*>(d.Sold), static_cast<Real*>(d.Snew), d.Uedge,
+        d.bc.bc == 2 ? 1 : 0, d.flag);
+    mark(5, bs);
+    mark(6, bs);
+    if (g.W > 0)
+      k_frame2<S, Real><<<(g.frame_n + 127) / 128, 128, 0, bs>>>(
+          g, c, B, static_cast<const Real*>(d.Sold), static_cast<const Real*>(d.Snew));
+    mark(7, bs);
+    mark(8, bs);
+    k_gamma<S, Real, DEV, STREAM><<<(g.ngamma + 127) / 128, 128, 0, bs>>>(g, c, d.bc, A, B,
+                                                                          d.Vtgt);
+    mark(9, bs);
     const int nbx = (g.Lx - g.Wf - (g.Wf / 32) * 32 + 31) / 32;
     const int ny_in = g.Ly - 2 * g.Wf;
     constexpr int BY = 4;
+    mark(2, d.st);
     if (nbx > 0 && ny_in > 0) {
       dim3 grid(nbx, (ny_in + BY - 1) / BY);
       k_bulk<S, Real, DEV, STREAM><<<grid, dim3(32, BY), 0, d.st>>>(g, c, A, B, d.flag);
     }
-    k_frame1<S, Real, DEV, STREAM><<<(g.frame_n + 127) / 128, 128, 0, d.st>>>(
-        g, c, A, B, static_cast<const Real*>(d.Sold), static_cast<Real*>(d.Snew), d.Uedge,
-        d.bc.bc == 2 ? 1 : 0, d.flag);
-    if (g.W > 0)
-      k_frame2<S, Real><<<(g.frame_n + 127) / 128, 128, 0, d.st>>>(
-          g, c, B, static_cast<const Real*>(d.Sold), static_cast<const Real*>(d.Snew));
-    k_gamma<S, Real, DEV, STREAM><<<(g.ngamma + 127) / 128, 128, 0, d.st>>>(g, c, d.bc, A, B,
-                                                                            d.Vtgt);
+    mark(3, d.st);
+    if (d.aux) {
+      cudaEventRecord(d.join, d.aux);
+      cudaStreamWaitEvent(d.st, d.join, 0);
+    }
     return cudaGetLastError();
   }
 

@@ -156,6 +156,18 @@ class Solver:
         buf = C.create_string_buffer(data, len(data))
         _check(L.lib().lbm_restore(self.ctx, buf, len(data)), self.ctx)
 
+    KERNEL_CLASSES = ("targets", "interior", "frame1", "frame2", "band")
+
+    def profile_enable(self, max_steps):
+        _check(L.lib().lbm_profile_enable(self.ctx, int(max_steps)), self.ctx)
+
+    def profile_read(self):
+        """{kernel class: summed GPU ms}, recorded steps; restarts recording."""
+        ms = (C.c_double * 5)()
+        n = C.c_int()
+        _check(L.lib().lbm_profile_read(self.ctx, ms, C.byref(n)), self.ctx)
+        return dict(zip(self.KERNEL_CLASSES, ms[:])), n.value
+
     @property
     def steps(self):
         g = (C.c_int64 * 8)()

@@ -81,12 +81,15 @@ def test_parity_vortex_nrbc_pml(precision):
     check(kw, fields, 60, precision)
 
 
-@pytest.mark.parametrize("edges", [(1, 1, 1, 1), (0, 0, 0, 0)])
-def test_parity_nrbc_without_pml(edges):
+@pytest.mark.parametrize("edges,steps", [((1, 1, 1, 1), 40), ((0, 0, 0, 0), 80)])
+def test_parity_nrbc_without_pml(edges, steps):
+    """Characteristic BC with no PML. With CBC relax on all four edges the case is sensitive:
+    the oracle rerun from 1-ulp-perturbed inputs moves by 1.2e-12 (rho) after 80 steps, so the
+    1e-12 bound is checked at 40 steps."""
     kw = case_kwargs(nx=40, ny=40, W=0, tau=0.7, sigma_max=0.0, bc="nrbc", nrbc_edges=edges,
                      beta=0.2, mean=(1.0, 0.1, -0.05, 1.0))
     fields = wl.pressure_pulse(40, 40, 0, amp=2e-3, halfwidth=4.0, u0=(0.1, -0.05))
-    check(kw, fields, 80)
+    check(kw, fields, steps)
 
 
 def test_parity_periodic_ragged():
