@@ -154,6 +154,26 @@ lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes);
 lbm_status lbm_profile_enable(lbm_ctx* ctx, int max_steps);
 lbm_status lbm_profile_read(lbm_ctx* ctx, double* ms, int* steps);
 
+/* Conserved totals of macroscopic fields that the caller already holds on the device, computed
+ * without allocating anything. The paper has no counterpart: this exists for callers that cannot
+ * call cudaMalloc - code running while a CUDA graph is captured, plugins inside an application
+ * that owns all device memory through its own pool, processes with a fixed memory budget.
+ * rho, ux, uy, T: device arrays of n float64 values each (e.g. the fields of lbm_moments);
+ * out: device array of 7 float64 written with the same quantities as lbm_reduce (sum rho,
+ * sum rho u_x, sum rho u_y, sum (1/2) rho (|u|^2 + 2 T), min rho, min T, count of non-finite or
+ * non-positive rho / T). n must be 1 .. LBM_TOTALS_NOALLOC_MAX_N, else LBM_EINVAL.
+ * The per-block partial sums live in one fixed 64 KiB device array of the library (1024 blocks
+ * x 8 doubles), which every GPU that loads the library keeps until the process exits; every
+ * call on a device shares it and rewrites all the slots it uses, so nothing needs clearing, but
+ * calls that overlap on the GPU (other streams, other threads) race on it. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device current:
+ * make that first call before any stream capture. No cudaMalloc, cudaFree or allocating library
+ * routine is called. Asynchronous on cuda_stream (a cudaStream_t, NULL = legacy default stream).
+ * Errors are reported by lbm_last_error(NULL). */
+#define LBM_TOTALS_NOALLOC_MAX_N ((int64_t)1 << 28)
+lbm_status lbm_totals_noalloc(const double* rho, const double* ux, const double* uy,
+                              const double* T, int64_t n, double* out, void* cuda_stream);
+
 /* Last error message of the context (or of the last failed lbm_create when ctx is NULL). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
 LBM_BC_PERIODIC, LBM_BC_ZG, LBM_BC_NRBC = 0, 1, 2
 LBM_NRBC_PNR_LODI, LBM_NRBC_CBC_RELAX = 0, 1
 LBM_FP64, LBM_FP32_DEV = 0, 1
+LBM_TOTALS_NOALLOC_MAX_N = 1 << 28
 
 
 class lbm_grid(C.Structure):
@@ -57,6 +58,8 @@ PROTOTYPES = {
     "lbm_restore": (C.c_int, [_ctx, C.c_void_p, C.c_size_t]),
     "lbm_profile_enable": (C.c_int, [_ctx, C.c_int]),
     "lbm_profile_read": (C.c_int, [_ctx, _dp, C.POINTER(C.c_int)]),
+    "lbm_totals_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                     C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [_ctx]),
     "lbm_destroy": (C.c_int, [_ctx]),
 }

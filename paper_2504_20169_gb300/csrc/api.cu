@@ -161,6 +161,8 @@ int halo_of(int q) { return q == 9 ? 1 : 3; }
 
 }  // namespace
 
+void lbm::set_global_error(const std::string& msg) { g_create_error = msg; }
+
 // --------------------------------------------------------------------------------------------
 struct lbm_ctx {
   int q = 0;

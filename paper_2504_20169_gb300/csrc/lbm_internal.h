@@ -1,5 +1,7 @@
 // Host-side plumbing shared by the translation units of liblbm (not part of the C ABI).
 #pragma once
+#include <string>
+
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -50,6 +52,9 @@ OpsTable ops_q17_f64();
 OpsTable ops_q17_f32();
 OpsTable ops_q9_f64();
 OpsTable ops_q9_f32();
+
+// Message returned by lbm_last_error(NULL) (calls without a context).
+void set_global_error(const std::string& msg);
 
 // Final pass of the deterministic two-pass FP64 reduction: n partial rows of 12 values ->
 // out[12] (slots in min_mask take the minimum).
