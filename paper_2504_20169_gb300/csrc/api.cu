@@ -365,7 +365,11 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   if (cudaHostGetDevicePointer((void**)&ctx->dflag, ctx->hflag, 0) != cudaSuccess)
     return oom("status flag mapping");
 
-  if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+  // the boundary chain is latency-bound: give its stream the highest priority so its blocks
+  // are scheduled ahead of the interior kernel's as SM slots free up
+  int prio_low = 0, prio_high = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  if (cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) != cudaSuccess ||
