@@ -334,19 +334,25 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
   const bool in_p = g.W > 0 && d < g.W;
   const Real sig = in_p ? sigma_at(c, g.W, d) : Real(0);
   const EqCoef<Real> k = eq_coef<S::ORDER, Real>(m);
+  if (has_q) {
+    // all accumulator loads in flight before any store
+    Real so[S::Q];
 #pragma unroll
-  for (int i = 0; i < S::Q; ++i) {
-    const Real eq = eq_dir<S, Real, DEV>(i, m, k, c);
-    Real out = p[i] + c.omega * (eq - p[i]);
-    if (has_q) {
+    for (int i = 0; i < S::Q; ++i) so[i] = __ldg(Sold + (long long)i * g.Sp + fi);
+#pragma unroll
+    for (int i = 0; i < S::Q; ++i) {
+      const Real eq = eq_dir<S, Real, DEV>(i, m, k, c);
       const Real fhat = eq - c.eqbar[i];
-      const long long si = (long long)i * g.Sp + fi;
-      const Real so = Sold[si];
-      const Real q = so + Real(0.5) * fhat;
-      Snew[si] = so + fhat;
+      const Real q = so[i] + Real(0.5) * fhat;
+      Snew[(long long)i * g.Sp + fi] = so[i] + fhat;
+      Real out = p[i] + c.omega * (eq - p[i]);
       if (in_p) out = out - sig * (Real(2) * fhat + sig * q);
+      B[(long long)i * g.plane + idx] = out;
     }
-    B[(long long)i * g.plane + idx] = out;
+  } else {
+    collide_bgk<S, Real, DEV>(p, m, c);
+#pragma unroll
+    for (int i = 0; i < S::Q; ++i) B[(long long)i * g.plane + idx] = p[i];
   }
 }
 
@@ -395,13 +401,15 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
     const Real* sn = Snew + (long long)i * g.Sp;
     Real gq = 0;
     if (S::ex(i) != 0) {
-      const Real dx = cx0 * (so[ax0] + sn[ax0]) + cx1 * (so[ax1] + sn[ax1]) +
-                      cx2 * (so[ax2] + sn[ax2]);
+      const Real dx = cx0 * (__ldg(so + ax0) + __ldg(sn + ax0)) +
+                      cx1 * (__ldg(so + ax1) + __ldg(sn + ax1)) +
+                      cx2 * (__ldg(so + ax2) + __ldg(sn + ax2));
       gq += Real(S::ex(i)) * dx;
     }
     if (S::ey(i) != 0) {
-      const Real dy = cy0 * (so[ay0] + sn[ay0]) + cy1 * (so[ay1] + sn[ay1]) +
-                      cy2 * (so[ay2] + sn[ay2]);
+      const Real dy = cy0 * (__ldg(so + ay0) + __ldg(sn + ay0)) +
+                      cy1 * (__ldg(so + ay1) + __ldg(sn + ay1)) +
+                      cy2 * (__ldg(so + ay2) + __ldg(sn + ay2));
       gq += Real(S::ey(i)) * dy;
     }
     Real* b = B + (long long)i * g.plane + idx;
@@ -483,16 +491,19 @@ __global__ void __launch_bounds__(128) k_gamma(Geom g, Consts<Real> c, BcParams 
 // ------------------------------------------------------------------------------------------
 // Characteristic targets (Sec. 4): one Runge-Kutta stage for every edge-band node.
 // ------------------------------------------------------------------------------------------
-struct Prim { double rho, un, ut, T; };
+template <class R>
+struct PrimT { R rho, un, ut, T; };
+using Prim = PrimT<double>;
 
 // Inverse of the characteristic map: given w = S dU (acoustic-, entropy, shear, acoustic+),
 // return dU = S^-1 w in (rho, u_n, u_t, T). With P = rho T (c_s = 1), c^2 = 2 T (gamma = 2):
 // dP = (w1 + w4)/2, du_n = (w4 - w1)/(2 rho c), du_t = w3, drho = (dP + w2)/c^2,
 // dT = (dP - T drho)/rho.
-__device__ inline Prim char_inverse(const Prim& U, double c, const double w[4]) {
-  Prim d;
-  const double dP = 0.5 * (w[0] + w[3]);
-  d.un = (w[3] - w[0]) / (2.0 * U.rho * c);
+template <class R>
+__device__ inline PrimT<R> char_inverse(const PrimT<R>& U, R c, const R w[4]) {
+  PrimT<R> d;
+  const R dP = R(0.5) * (w[0] + w[3]);
+  d.un = (w[3] - w[0]) / (R(2) * U.rho * c);
   d.ut = w[2];
   d.rho = (dP + w[1]) / (c * c);
   d.T = (dP - U.T * d.rho) / U.rho;
@@ -501,8 +512,9 @@ __device__ inline Prim char_inverse(const Prim& U, double c, const double w[4]) 
 
 // w = S dU for the normal axis: w1 = T drho - rho c du_n + rho dT, w2 = T drho - rho dT,
 // w3 = du_t, w4 = T drho + rho c du_n + rho dT (left eigenvectors of the Euler Jacobian).
-__device__ inline void char_forward(const Prim& U, double c, const Prim& dU, double w[4]) {
-  const double dP = U.T * dU.rho + U.rho * dU.T;
+template <class R>
+__device__ inline void char_forward(const PrimT<R>& U, R c, const PrimT<R>& dU, R w[4]) {
+  const R dP = U.T * dU.rho + U.rho * dU.T;
   w[0] = dP - U.rho * c * dU.un;
   w[1] = U.T * dU.rho - U.rho * dU.T;
   w[2] = dU.ut;
@@ -519,9 +531,11 @@ __device__ inline Prim load_prim(const double* V, int stride, int slot, bool xax
   return u;
 }
 
-// stage 1..4 of classical RK4 over one time step; fluid moments Ue frozen at time n.
-__global__ void k_nrbc_stage(Geom g, BcParams bc, const double* __restrict__ Ue,
-                             double* __restrict__ V0, const double* __restrict__ Vin,
-                             double* __restrict__ Vout, double* __restrict__ acc, int stage);
+template <class R>
+__device__ inline PrimT<R> to(const Prim& p) {
+  return PrimT<R>{R(p.rho), R(p.un), R(p.ut), R(p.T)};
+}
+
+
 
 }  // namespace lbm

@@ -53,6 +53,10 @@ OpsTable ops_q17_f32();
 OpsTable ops_q9_f64();
 OpsTable ops_q9_f32();
 
+// Characteristic-target RK4 stages of one step on stream s; fp32 selects FP32 characteristic
+// algebra (targets and differences stay FP64).
+cudaError_t launch_nrbc_stages(const Dev& d, bool fp32, cudaStream_t s);
+
 // Message returned by lbm_last_error(NULL) (calls without a context).
 void set_global_error(const std::string& msg);
 

@@ -5,12 +5,15 @@
 
 namespace lbm {
 
+// stage 1..4 of classical RK4 over one time step; fluid moments Ue frozen at time n. Targets,
+// stage values and all differences are FP64; the characteristic algebra runs in R.
 // One stage of classical RK4 for dU/dt of every edge-band node (fluid moments Ue frozen at
 // time n). Band node b -> edge (W, E, S, N), layer j = 1..M outward, tangential index t.
 // Rates: Eq. (thermal_LODI_macro_evo) with Eq. (PNR) for PNR-LODI edges, Eq.
 // (thermal_CBC_macro_evo) with Eq. (CBC-Relax) for CBC-relax edges; viscous part zero.
 // Derivatives per node index: normal one-sided 2nd order toward the outside, tangential
 // central (one-sided at the band ends); one node is r normalized lengths.
+template <class R>
 __global__ void k_nrbc_stage(Geom g, BcParams bc, const double* __restrict__ Ue,
                              double* __restrict__ V0, const double* __restrict__ Vin,
                              double* __restrict__ Vout, double* __restrict__ acc, int stage) {
@@ -29,63 +32,64 @@ __global__ void k_nrbc_stage(Geom g, BcParams bc, const double* __restrict__ Ue,
   const int nb = g.nb, ne = g.ne;
   auto node = [&](int jj, int tt) { return off + (jj - 1) * len + tt; };
 
-  const Prim U0 = load_prim(Vin, nb, b, xaxis);
+  const Prim U0d = load_prim(Vin, nb, b, xaxis);
   const Prim U1 = j >= 2 ? load_prim(Vin, nb, node(j - 1, t), xaxis)
                          : load_prim(Ue, ne, ueoff + t, xaxis);
   const Prim U2 = j >= 3 ? load_prim(Vin, nb, node(j - 2, t), xaxis)
                          : (j == 2 ? load_prim(Ue, ne, ueoff + t, xaxis)
                                    : load_prim(Ue, ne, ueoff + len + t, xaxis));
-  const double inv_r = 1.0 / bc.r;
-  // d/dx_axis (per node) = out * (3 U(x_b) - 4 U(x_b - n) + U(x_b - 2n)) / 2, then / r
-  Prim dn;
-  dn.rho = out * 0.5 * (3.0 * U0.rho - 4.0 * U1.rho + U2.rho) * inv_r;
-  dn.un = out * 0.5 * (3.0 * U0.un - 4.0 * U1.un + U2.un) * inv_r;
-  dn.ut = out * 0.5 * (3.0 * U0.ut - 4.0 * U1.ut + U2.ut) * inv_r;
-  dn.T = out * 0.5 * (3.0 * U0.T - 4.0 * U1.T + U2.T) * inv_r;
+  // d/dx_axis per node = out * (3 U(x_b) - 4 U(x_b - n) + U(x_b - 2n)) / 2; differences in FP64
+  const double hs = 0.5 * out;
+  PrimT<R> dn;
+  dn.rho = R(hs * (3.0 * U0d.rho - 4.0 * U1.rho + U2.rho));
+  dn.un = R(hs * (3.0 * U0d.un - 4.0 * U1.un + U2.un));
+  dn.ut = R(hs * (3.0 * U0d.ut - 4.0 * U1.ut + U2.ut));
+  dn.T = R(hs * (3.0 * U0d.T - 4.0 * U1.T + U2.T));
 
-  const double c = sqrt(2.0 * U0.T);  // gamma T with gamma = (D + 2) / D = 2
-  const double lam[4] = {U0.un - c, U0.un, U0.un, U0.un + c};
-  double wn[4];
+  const PrimT<R> U0 = to<R>(U0d);
+  const R inv_r = R(1.0 / bc.r);
+  const R c = sqrt(R(2) * U0.T);  // gamma T with gamma = (D + 2) / D = 2
+  const R lam[4] = {U0.un - c, U0.un, U0.un, U0.un + c};
+  R wn[4];
   char_forward(U0, c, dn, wn);
-  double L[4];
-  for (int k = 0; k < 4; ++k) L[k] = lam[k] * wn[k];
-
-  double tot[4];
+  const R sgn = R(out);
+  R tot[4];
   if (bc.edge[e] == 0) {
     // PNR-LODI: incoming amplitudes vanish, transverse terms dropped
-    for (int k = 0; k < 4; ++k) tot[k] = (lam[k] * out < 0.0) ? 0.0 : L[k];
+    for (int k = 0; k < 4; ++k) tot[k] = (lam[k] * sgn < R(0)) ? R(0) : lam[k] * wn[k] * inv_r;
   } else {
     // CBC relax: transverse amplitudes T = S B dU/dt_axis
-    Prim dt;
-    const Prim Va = load_prim(Vin, nb, node(j, t == 0 ? 0 : (t == len - 1 ? t - 2 : t - 1)), xaxis);
-    const Prim Vb = load_prim(Vin, nb, node(j, t == 0 ? 1 : (t == len - 1 ? t - 1 : t)), xaxis);
-    const Prim Vc = load_prim(Vin, nb, node(j, t == 0 ? 2 : (t == len - 1 ? t : t + 1)), xaxis);
+    const int ta = t == 0 ? 0 : (t == len - 1 ? t - 2 : t - 1);
+    const Prim Va = load_prim(Vin, nb, node(j, ta), xaxis);
+    const Prim Vb = load_prim(Vin, nb, node(j, ta + 1), xaxis);
+    const Prim Vc = load_prim(Vin, nb, node(j, ta + 2), xaxis);
     double ca, cb, cc;
     if (t == 0) { ca = -1.5; cb = 2.0; cc = -0.5; }
     else if (t == len - 1) { ca = 0.5; cb = -2.0; cc = 1.5; }
     else { ca = -0.5; cb = 0.0; cc = 0.5; }
-    dt.rho = (ca * Va.rho + cb * Vb.rho + cc * Vc.rho) * inv_r;
-    dt.un = (ca * Va.un + cb * Vb.un + cc * Vc.un) * inv_r;
-    dt.ut = (ca * Va.ut + cb * Vb.ut + cc * Vc.ut) * inv_r;
-    dt.T = (ca * Va.T + cb * Vb.T + cc * Vc.T) * inv_r;
+    PrimT<R> dt;
+    dt.rho = R(ca * Va.rho + cb * Vb.rho + cc * Vc.rho);
+    dt.un = R(ca * Va.un + cb * Vb.un + cc * Vc.un);
+    dt.ut = R(ca * Va.ut + cb * Vb.ut + cc * Vc.ut);
+    dt.T = R(ca * Va.T + cb * Vb.T + cc * Vc.T);
     // B dU along the tangential axis (tangential velocity u_t advects; P_t = T rho_t + rho T_t)
-    Prim bd;
+    PrimT<R> bd;
     bd.rho = U0.ut * dt.rho + U0.rho * dt.ut;
     bd.un = U0.ut * dt.un;
     bd.ut = (U0.T / U0.rho) * dt.rho + U0.ut * dt.ut + dt.T;
     bd.T = U0.T * dt.ut + U0.ut * dt.T;  // (2/D) T with D = 2
-    double Tc[4];
+    R Tc[4];
     char_forward(U0, c, bd, Tc);
-    const double relax = (bc.relax_sign == 0.0 ? -1.0 : bc.relax_sign) * (1.0 - bc.beta);
+    const R relax = R((bc.relax_sign == 0.0 ? -1.0 : bc.relax_sign) * (1.0 - bc.beta));
     for (int k = 0; k < 4; ++k) {
-      const double Lbar = (lam[k] * out < 0.0) ? relax * Tc[k] : L[k];
-      tot[k] = Lbar + Tc[k];
+      const R Lbar = (lam[k] * sgn < R(0)) ? relax * Tc[k] : lam[k] * wn[k];
+      tot[k] = (Lbar + Tc[k]) * inv_r;
     }
   }
-  const Prim r = char_inverse(U0, c, tot);
+  const PrimT<R> r = char_inverse(U0, c, tot);
   // rate k = -S^-1 (...) in (rho, u_x, u_y, T)
-  const double k0 = -r.rho, k3 = -r.T;
-  const double kx = xaxis ? -r.un : -r.ut, ky = xaxis ? -r.ut : -r.un;
+  const double k0 = -double(r.rho), k3 = -double(r.T);
+  const double kx = xaxis ? -double(r.un) : -double(r.ut), ky = xaxis ? -double(r.ut) : -double(r.un);
   const double kk[4] = {k0, kx, ky, k3};
   if (stage < 4) {
     const double a = stage == 3 ? 1.0 : 0.5;
@@ -97,6 +101,24 @@ __global__ void k_nrbc_stage(Geom g, BcParams bc, const double* __restrict__ Ue,
   } else {
     for (int q = 0; q < 4; ++q) V0[q * nb + b] = V0[q * nb + b] + (acc[q * nb + b] + kk[q]) / 6.0;
   }
+}
+
+// The four RK4 stages of one step (buffers: stage input Vtgt -> Va -> Vb -> Va; Vtgt updated in
+// place by the last stage).
+cudaError_t launch_nrbc_stages(const Dev& d, bool fp32, cudaStream_t s) {
+  const Geom& g = d.g;
+  const int nbk = (g.nb + 127) / 128;
+  const double* Vin[4] = {d.Vtgt, d.Va, d.Vb, d.Va};
+  double* Vout[4] = {d.Va, d.Vb, d.Va, nullptr};
+  for (int k = 1; k <= 4; ++k) {
+    if (fp32)
+      k_nrbc_stage<float><<<nbk, 128, 0, s>>>(g, d.bc, d.Uedge, d.Vtgt, Vin[k - 1], Vout[k - 1],
+                                               d.Vacc, k);
+    else
+      k_nrbc_stage<double><<<nbk, 128, 0, s>>>(g, d.bc, d.Uedge, d.Vtgt, Vin[k - 1], Vout[k - 1],
+                                                d.Vacc, k);
+  }
+  return cudaGetLastError();
 }
 
 __global__ void k_reduce_final(const double* __restrict__ partials, int n, unsigned min_mask,

@@ -188,14 +188,7 @@ struct Ops {
       cudaStreamWaitEvent(d.aux, d.fork, 0);
     }
     mark(0, bs);
-    if (STREAM && d.bc.bc == 2) {
-      const int nbk = (g.nb + 127) / 128;
-      const double* Vin[4] = {d.Vtgt, d.Va, d.Vb, d.Va};
-      double* Vout[4] = {d.Va, d.Vb, d.Va, nullptr};
-      for (int s = 1; s <= 4; ++s)
-        k_nrbc_stage<<<nbk, 128, 0, bs>>>(g, d.bc, d.Uedge, d.Vtgt, Vin[s - 1], Vout[s - 1],
-                                          d.Vacc, s);
-    }
+    if (STREAM && d.bc.bc == 2) launch_nrbc_stages(d, sizeof(Real) == 4, bs);
     mark(1, bs);
     mark(4, bs);
     k_frame1<S, Real, DEV, STREAM><<<(g.frame_n + 127) / 128, 128, 0, bs>>>(
