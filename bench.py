@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--window", type=int, default=200,
                     help="steps per fresh solve; the printed PML stays finite on this workload "
                          "for about 300 steps (tau 0.55), so timed steps run in windows")
+    ap.add_argument("--serving", type=int, default=1,
+                    help="also run the batched sweep and the serving stream (0 skips)")
     ap.add_argument("--size", type=int, default=2048,
                     help="bulk edge (2048 = the workload; smaller sizes for profiler captures)")
     return ap.parse_args()
@@ -212,6 +214,33 @@ def timed_run(Solver, c, fields, precision, steps, warmup, dev, window, prof_ste
     return total, per, prof, ck, tot
 
 
+def serving_runs(args):
+    """Batched sweep (32 seeded uneven instances, all admitted at t = 0, 150 steps each) and a
+    seeded Poisson request stream (48 requests at 50/s, bulk 64..1024, 100..300 steps), both in
+    FP32 deviation storage through the continuous-batching loop."""
+    import workloads as wl
+    from paper_2504_20169_gb300.serving import Engine, Request, summarize
+    sweep = wl.batched_sweep(count=32, seed=0, steps=150)
+    reqs = [Request(k, 0.0, c, c.steps) for k, c in enumerate(sweep)]
+    eng = Engine(budget_bytes=100e9, precision="fp32dev", chunk=150, keep_fields=False)
+    eng.run(reqs)
+    eng.close()
+    b = summarize(reqs, eng.wall, eng.sites_steps)
+    b["what"] = "32 instances of the seeded batched sweep (N 128..1024, W 4..64, ZG/NRBC, " \
+                "pulse/vortex), 150 steps each, one combined graph per step; wall clock " \
+                "includes admission (host IC + upload) and retirement"
+    stream = wl.request_stream(48, rate=50.0, seed=0, nmax=1024, smin=100, smax=300)
+    reqs = [Request(k, t, c, c.steps) for k, (t, c) in enumerate(stream)]
+    eng = Engine(budget_bytes=40e9, precision="fp32dev", chunk=50, keep_fields=False)
+    eng.run(reqs)
+    eng.close()
+    sv = summarize(reqs, eng.wall, eng.sites_steps)
+    sv["what"] = "Poisson stream 50/s, 48 requests, bulk log-uniform 64..1024, PML 8..64, " \
+                 "100..300 steps, 40 GB admission budget, chunks of 50 steps; latency from " \
+                 "arrival to fields on the host"
+    return b, sv
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -311,6 +340,10 @@ def main():
            "what": f"{nrep} solves through the C ABI: lbm_init from pinned host fields, "
                    f"{args.window} steps, lbm_moments to pinned host; wall clock"}
 
+    batched = serving = None
+    if args.serving:
+        batched, serving = serving_runs(args)
+
     if rank == 0:
         cpu = oracle_sample(args.cpu_seconds) if args.cpu_seconds > 0 else None
         per_sorted = sorted(per)
@@ -328,7 +361,8 @@ def main():
                        f"replicas x{ws}"},
             "latency_ms": {"p50": round(statistics.median(per), 5),
                            "p99": round(per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)], 5)},
-            "roofline": roof, "fp64": fp64, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roof, "fp64": fp64, "batched_fp32": batched, "serving": serving,
+            "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": args.steps * (8 if c.W > 0 else 7), "clocks": ck,
             "timing": f"headline: fresh solves of {args.window} steps (untimed re-init between), "
                       "CUDA-graph replay, events per step on the launching stream; roofline: "

@@ -154,6 +154,27 @@ lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes);
 lbm_status lbm_profile_enable(lbm_ctx* ctx, int max_steps);
 lbm_status lbm_profile_read(lbm_ctx* ctx, double* ms, int* steps);
 
+/* Device bytes lbm_create would allocate for these arguments (no allocation, no GPU needed);
+ * used for admission by HBM budget. Returns LBM_EINVAL for arguments lbm_create rejects. */
+lbm_status lbm_estimate_bytes(const lbm_grid* grid, lbm_stencil stencil, int pml_width,
+                              lbm_bc_kind bc, lbm_precision precision, size_t* bytes);
+
+/* Batched execution of independent instances (serving). A batch holds a resident set of
+ * initialized contexts on one device and advances all of them together: each step is one
+ * CUDA-graph launch on the batch's stream whose child graphs are the members' own one-step
+ * graphs, so instances of different sizes, PML widths and boundary conditions overlap on the
+ * GPU while every member computes exactly what lbm_step would (bit-identical results).
+ * lbm_batch_set replaces the resident set (continuous batching: call it between steps as
+ * instances are admitted or retired; the combined graph is rebuilt on the next step).
+ * lbm_batch_step returns LBM_EUNSTABLE without stepping anyone if a member has flagged an
+ * unphysical state (find it with lbm_sync, drop it with lbm_batch_set). The batch does not own
+ * its members; destroy a context only after removing it from every batch. */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(void* cuda_stream, lbm_batch** out);
+lbm_status lbm_batch_set(lbm_batch* batch, lbm_ctx* const* ctxs, int count);
+lbm_status lbm_batch_step(lbm_batch* batch, int n);
+lbm_status lbm_batch_destroy(lbm_batch* batch);
+
 /* Conserved totals of macroscopic fields that the caller already holds on the device, computed
  * without allocating anything. The paper has no counterpart: this exists for callers that cannot
  * call cudaMalloc - code running while a CUDA graph is captured, plugins inside an application

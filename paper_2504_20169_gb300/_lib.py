@@ -58,6 +58,12 @@ PROTOTYPES = {
     "lbm_restore": (C.c_int, [_ctx, C.c_void_p, C.c_size_t]),
     "lbm_profile_enable": (C.c_int, [_ctx, C.c_int]),
     "lbm_profile_read": (C.c_int, [_ctx, _dp, C.POINTER(C.c_int)]),
+    "lbm_estimate_bytes": (C.c_int, [C.POINTER(lbm_grid), C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.POINTER(C.c_size_t)]),
+    "lbm_batch_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lbm_batch_set": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
+    "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
     "lbm_totals_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                      C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [_ctx]),

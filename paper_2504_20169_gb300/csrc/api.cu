@@ -192,6 +192,7 @@ struct lbm_ctx {
   cudaStream_t aux = nullptr, cap = nullptr;   // boundary-chain stream, capture stream
   cudaEvent_t fork = nullptr, join = nullptr, ready = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one step, keyed by the buffer parity
+  cudaGraph_t gtemplate[2] = {nullptr, nullptr};  // the captured graphs (child graphs of batches)
   bool use_graphs = true;
   std::vector<cudaEvent_t> prof;   // kKernelClasses * 2 events per recorded step
   int prof_cap = 0, prof_used = 0;
@@ -213,8 +214,10 @@ static void free_all(lbm_ctx* ctx) {
   if (ctx->st) cudaStreamSynchronize(ctx->st); else cudaDeviceSynchronize();
   for (cudaEvent_t e : ctx->prof) cudaEventDestroy(e);
   ctx->prof.clear();
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < 2; ++k) {
     if (ctx->graph[k]) cudaGraphExecDestroy(ctx->graph[k]);
+    if (ctx->gtemplate[k]) cudaGraphDestroy(ctx->gtemplate[k]);
+  }
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   if (ctx->fork) cudaEventDestroy(ctx->fork);
@@ -263,6 +266,47 @@ lbm_status lbm_lattice_info(lbm_stencil stencil, int* q, int* e, double* w, doub
   return LBM_OK;
 }
 
+// Storage geometry of a grid (section "Storage" of lbm_device.cuh) and the bytes it needs.
+static Geom make_geom(int nx, int ny, int W, int M) {
+  Geom g{};
+  g.nx = nx;
+  g.ny = ny;
+  g.W = W;
+  g.M = M;
+  g.Lx = nx + 2 * W;
+  g.Ly = ny + 2 * W;
+  g.cF0 = 32;
+  g.pitch = ((g.cF0 + g.Lx + g.M) + 31) / 32 * 32;
+  g.plane = ((long long)g.pitch * (g.Ly + 2 * g.M) + 63) / 64 * 64;
+  g.Wf = g.W > 0 ? std::max(g.W + 1, g.M) : g.M;
+  g.frame_n = 2 * g.Wf * g.Lx + 2 * (g.Ly - 2 * g.Wf) * g.Wf;
+  g.Sp = g.W > 0 ? ((long long)g.frame_n + 31) / 32 * 32 : 0;
+  g.nb = 2 * g.M * (g.Lx + g.Ly);
+  g.ne = 4 * (g.Lx + g.Ly);
+  g.ngamma = 2 * g.M * (g.Lx + 2 * g.M) + 2 * g.M * g.Ly;
+  return g;
+}
+
+static size_t bytes_of(const Geom& g, int q, int es) {
+  const size_t max_blocks = (size_t)((g.Lx + 31) / 32) * ((g.Ly + 7) / 8);
+  return 2 * (size_t)q * g.plane * es + 2 * (size_t)q * g.Sp * es +
+         sizeof(double) * (16 * (size_t)g.nb + 4 * (size_t)g.ne + 4 * (size_t)g.Lx * g.Ly +
+                           12 * max_blocks + 16);
+}
+
+extern "C" lbm_status lbm_estimate_bytes(const lbm_grid* grid, lbm_stencil stencil, int pml_width,
+                                         lbm_bc_kind bc, lbm_precision precision, size_t* bytes) {
+  if (!grid || !bytes) return LBM_EINVAL;
+  const int q = (int)stencil;
+  if ((q != 37 && q != 17 && q != 9) || grid->nx < 8 || grid->ny < 8 || pml_width < 0 ||
+      pml_width == 1 || (bc == LBM_BC_PERIODIC && pml_width != 0) ||
+      (precision != LBM_FP64 && precision != LBM_FP32_DEV))
+    return LBM_EINVAL;
+  const Geom g = make_geom(grid->nx, grid->ny, pml_width, halo_of(q));
+  *bytes = bytes_of(g, q, precision == LBM_FP64 ? 8 : 4);
+  return LBM_OK;
+}
+
 lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int pml_width,
                       const lbm_sigma_profile* sigma, lbm_bc_kind bc, const lbm_bc_params* bcp,
                       lbm_precision precision, void* cuda_stream, lbm_ctx** out) {
@@ -304,22 +348,8 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   if (!lattice_of(q, ctx->w, &ctx->r, lerr)) { delete ctx; return fail("quadrature failed"); }
   cudaGetDevice(&ctx->device);
 
+  ctx->g = make_geom(grid->nx, grid->ny, pml_width, halo_of(q));
   Geom& g = ctx->g;
-  g.nx = grid->nx;
-  g.ny = grid->ny;
-  g.W = pml_width;
-  g.M = halo_of(q);
-  g.Lx = g.nx + 2 * g.W;
-  g.Ly = g.ny + 2 * g.W;
-  g.cF0 = 32;
-  g.pitch = ((g.cF0 + g.Lx + g.M) + 31) / 32 * 32;
-  g.plane = ((long long)g.pitch * (g.Ly + 2 * g.M) + 63) / 64 * 64;
-  g.Wf = g.W > 0 ? std::max(g.W + 1, g.M) : g.M;
-  g.frame_n = 2 * g.Wf * g.Lx + 2 * (g.Ly - 2 * g.Wf) * g.Wf;
-  g.Sp = g.W > 0 ? ((long long)g.frame_n + 31) / 32 * 32 : 0;
-  g.nb = 2 * g.M * (g.Lx + g.Ly);
-  g.ne = 4 * (g.Lx + g.Ly);
-  g.ngamma = 2 * g.M * (g.Lx + 2 * g.M) + 2 * g.M * g.Ly;
 
   switch (q * 2 + (precision == LBM_FP32_DEV)) {
     case 74: ctx->ops = ops_q37_f64(); break;
@@ -506,8 +536,9 @@ static lbm_status build_graph(lbm_ctx* ctx, int parity) {
   LBM_CK(e);
   LBM_CK(e2);
   e = cudaGraphInstantiate(&ctx->graph[parity], graph, 0);
-  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) cudaGraphDestroy(graph);
   LBM_CK(e);
+  ctx->gtemplate[parity] = graph;
   return LBM_OK;
 }
 
@@ -727,6 +758,103 @@ lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes) {
   ctx->prev_prestream = (h.flags & 2) != 0;
   ctx->initialized = true;
   *ctx->hflag = 0;
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+// --------------------------------------------------------------------------------------------
+// Batched execution: one combined graph per step over the resident set (see lbm.h).
+struct lbm_batch {
+  cudaStream_t st = nullptr;
+  std::vector<lbm_ctx*> members;
+  // combined executable graphs keyed by the members' buffer parities at launch time
+  std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> cache;
+  std::string err;
+};
+
+static void batch_clear(lbm_batch* b) {
+  for (auto& e : b->cache) cudaGraphExecDestroy(e.second);
+  b->cache.clear();
+}
+
+extern "C" {
+
+lbm_status lbm_batch_create(void* cuda_stream, lbm_batch** out) {
+  if (!out) return LBM_EINVAL;
+  lbm_batch* b = new lbm_batch();
+  b->st = (cudaStream_t)cuda_stream;
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set(lbm_batch* b, lbm_ctx* const* ctxs, int count) {
+  if (!b || count < 0 || (count > 0 && !ctxs)) return LBM_EINVAL;
+  int dev = -1;
+  for (int k = 0; k < count; ++k) {
+    if (!ctxs[k] || !ctxs[k]->initialized) { b->err = "batch member not initialized"; return LBM_ESTATE; }
+    if (dev >= 0 && ctxs[k]->device != dev) { b->err = "batch members on different devices"; return LBM_EINVAL; }
+    dev = ctxs[k]->device;
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) { b->err = "context listed twice"; return LBM_EINVAL; }
+  }
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) { b->err = "stream sync failed"; return LBM_ECUDA; }
+  batch_clear(b);
+  b->members.assign(ctxs, ctxs + count);
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int n) {
+  if (!b || n < 0) return LBM_EINVAL;
+  if (b->members.empty() || n == 0) return LBM_OK;
+  for (lbm_ctx* c : b->members)
+    if (*(volatile int*)c->hflag) { b->err = "a member flagged an unphysical state"; return LBM_EUNSTABLE; }
+  lbm_ctx* ctx = b->members[0];  // for LBM_CK messages
+  LBM_CK(cudaSetDevice(ctx->device));
+  for (int k = 0; k < n; ++k) {
+    std::vector<int> key;
+    key.reserve(b->members.size());
+    for (lbm_ctx* c : b->members) key.push_back(c->cur);
+    cudaGraphExec_t exec = nullptr;
+    for (auto& e : b->cache)
+      if (e.first == key) exec = e.second;
+    if (!exec) {
+      for (lbm_ctx* c : b->members)
+        if (!c->gtemplate[c->cur]) {
+          lbm_status gs = build_graph(c, c->cur);
+          if (gs != LBM_OK) { b->err = c->err; return gs; }
+        }
+      cudaGraph_t g = nullptr;
+      LBM_CK(cudaGraphCreate(&g, 0));
+      cudaError_t e = cudaSuccess;
+      for (lbm_ctx* c : b->members) {
+        cudaGraphNode_t node;
+        e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, c->gtemplate[c->cur]);
+        if (e != cudaSuccess) break;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      LBM_CK(e);
+      if (b->cache.size() >= 4) batch_clear(b);
+      b->cache.emplace_back(key, exec);
+    }
+    LBM_CK(cudaGraphLaunch(exec, b->st));
+    for (lbm_ctx* c : b->members) {
+      c->cur ^= 1;
+      c->scur ^= 1;
+      c->steps++;
+      c->prev_valid = true;
+      c->prev_prestream = false;
+    }
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return LBM_OK;
+  cudaStreamSynchronize(b->st);
+  batch_clear(b);
+  delete b;
   return LBM_OK;
 }
 
