@@ -128,6 +128,16 @@ class Clocks:
                 "samples": len(sm), "reasons": reasons}
 
 
+def max_over_ranks(x, dist=None, device=None):
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -273,11 +283,7 @@ def main():
                                           local, args.window,
                                           prof_steps=min(args.steps, args.window))
     barrier()
-    t_max = total
-    if dist is not None:
-        t = torch.tensor([total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(total, dist, "cuda")
     ms_step = t_max / args.steps
     value = ws * sites / (ms_step * 1e-3) / 1e6
 
@@ -295,6 +301,16 @@ def main():
             "kernel_share": {k: round(v / max(1e-9, sum(prof[0].values())), 4)
                              for k, v in prof[0].items()}}
     step_bytes = sites * 2 * 37 * 4
+    # algorithmic bytes of one whole step (FP32): interior nodes 2 x 37 x 4 B; frame nodes
+    # (PML + inner ring) also read and write the accumulator: 4 x 37 x 4 B; boundary layers
+    # outside F are written once: 37 x 4 B
+    frame_nodes = 2 * Wf * Lx + 2 * (Lx - 2 * Wf) * Wf
+    band_nodes = 2 * 3 * (Lx + 6) + 2 * 3 * Lx
+    alg_step = interior * 296 + frame_nodes * 592 + band_nodes * 148
+    step_roof = {"alg_bytes_per_step": alg_step,
+                 "achieved": round(alg_step / (ms_step * 1e-3) / 1e9, 1),
+                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": round(alg_step / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
     fp64 = None
     if not args.no_fp64:
         k64 = max(20, args.steps // 8)
@@ -329,10 +345,7 @@ def main():
     e2e_s = time.perf_counter() - t0
     barrier()
     s.close()
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     field_bytes = 4 * sites * 8
     e2e = {"value": round(ws * sites * nrep * args.window / e2e_s / 1e6, 1), "unit": "MLUPS",
            "h2d_bytes_per_step": field_bytes / args.window,
@@ -361,12 +374,13 @@ def main():
                        f"replicas x{ws}"},
             "latency_ms": {"p50": round(statistics.median(per), 5),
                            "p99": round(per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)], 5)},
-            "roofline": roof, "fp64": fp64, "batched_fp32": batched, "serving": serving,
+            "roofline": roof, "step_roofline": step_roof, "fp64": fp64, "batched_fp32": batched, "serving": serving,
             "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": args.steps * (8 if c.W > 0 else 7), "clocks": ck,
             "timing": f"headline: fresh solves of {args.window} steps (untimed re-init between), "
                       "CUDA-graph replay, events per step on the launching stream; roofline: "
-                      "interior kernel events in a separate directly launched window",
+                      "interior kernel events in a separate window where each kernel class "
+                      "runs alone; step_roofline: whole-step algorithmic bytes / ms_per_step",
             "totals_check": {"mass": float(tot[0]), "bad_nodes": float(tot[6])},
         }
         print(json.dumps(line), flush=True)

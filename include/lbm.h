@@ -149,7 +149,9 @@ lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes);
 /* Per-kernel timing (tracing). lbm_profile_enable(ctx, max_steps) makes the next max_steps
  * steps record CUDA events on the context stream around each kernel class: 0 characteristic
  * targets, 1 interior (BGK only), 2 PML frame phase 1, 3 PML frame phase 2, 4 boundary band;
- * max_steps = 0 disables. lbm_profile_read synchronizes, writes the summed GPU milliseconds of
+ * max_steps = 0 disables. Recorded steps are launched directly with every class running alone
+ * (no concurrency between the interior kernel and the boundary chain), so each class's time
+ * is its own; unrecorded steps keep the concurrent graph replay. lbm_profile_read synchronizes, writes the summed GPU milliseconds of
  * each class into ms[5] and the number of recorded steps into *steps, and restarts recording. */
 lbm_status lbm_profile_enable(lbm_ctx* ctx, int max_steps);
 lbm_status lbm_profile_read(lbm_ctx* ctx, double* ms, int* steps);

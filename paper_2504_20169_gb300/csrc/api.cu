@@ -422,6 +422,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   d.bc.beta = bp.beta;
   d.bc.relax_sign = bp.relax_sign == 0.0 ? -1.0 : bp.relax_sign;
   d.bc.r = ctx->r;
+  d.bc.inv_r = 1.0 / ctx->r;
   d.bc.omega = ctx->omega;
   double fbar[kMaxQ];
   if (q == 37) mean_equilibrium<D2Q37>(ctx->w, ctx->r, bp, fbar);
@@ -557,10 +558,14 @@ lbm_status lbm_step(lbm_ctx* ctx, int n) {
       LBM_CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->st));
     } else {
       set_roles(ctx, ctx->cur, ctx->scur);
-      ctx->dev.ev = nullptr;
-      if (profiled) ctx->dev.ev = &ctx->prof[(size_t)2 * kKernelClasses * ctx->prof_used++];
-      LBM_CK(ctx->ops.step(ctx->dev, true));
-      ctx->dev.ev = nullptr;
+      Dev d = ctx->dev;
+      if (profiled) {
+        // attribution: each kernel class runs alone (boundary chain after the interior kernel on
+        // one stream), so its events measure that class and nothing concurrent
+        d.ev = &ctx->prof[(size_t)2 * kKernelClasses * ctx->prof_used++];
+        d.aux = nullptr;
+      }
+      LBM_CK(ctx->ops.step(d, true));
     }
     ctx->cur ^= 1;
     ctx->scur ^= 1;

@@ -53,7 +53,7 @@ struct Consts {
 struct BcParams {
   int bc;            // 0 periodic, 1 zero gradient, 2 characteristic
   int edge[4];       // W E S N: 0 PNR-LODI, 1 CBC relax
-  double beta, relax_sign, r, omega;
+  double beta, relax_sign, r, omega, inv_r;
 };
 
 __host__ __device__ inline long long gindex(const Geom& g, int x, int y) {
@@ -112,14 +112,20 @@ struct Macro {
 // Eq. (macro) on stored values p (absolute f, or g = f - w when DEV).
 template <class S, class Real, bool DEV>
 __host__ __device__ inline Macro<Real> moments(const Real (&p)[S::Q], const Consts<Real>& c) {
-  Real s0 = 0, sx = 0, sy = 0, s2 = 0;
+  // column sums cx[k] = sum of p_i with e_ix = k and row sums cy[k] (k = -3..3): every moment
+  // below follows from them (rho, sum p e_x, sum p e_x^2 and the y counterparts)
+  Real cx[7] = {0, 0, 0, 0, 0, 0, 0}, cy[7] = {0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) {
-    s0 += p[i];
-    if (S::ex(i) != 0) sx += Real(S::ex(i)) * p[i];
-    if (S::ey(i) != 0) sy += Real(S::ey(i)) * p[i];
-    if (i != 0) s2 += Real(e2_of<S>(i)) * p[i];
+    cx[S::ex(i) + 3] += p[i];
+    cy[S::ey(i) + 3] += p[i];
   }
+  const Real s0 = ((cx[0] + cx[6]) + (cx[1] + cx[5])) + ((cx[2] + cx[4]) + cx[3]);
+  const Real sx = (cx[4] - cx[2]) + Real(2) * (cx[5] - cx[1]) + Real(3) * (cx[6] - cx[0]);
+  const Real sy = (cy[4] - cy[2]) + Real(2) * (cy[5] - cy[1]) + Real(3) * (cy[6] - cy[0]);
+  const Real sxx = (cx[4] + cx[2]) + Real(4) * (cx[5] + cx[1]) + Real(9) * (cx[6] + cx[0]);
+  const Real syy = (cy[4] + cy[2]) + Real(4) * (cy[5] + cy[1]) + Real(9) * (cy[6] + cy[0]);
+  const Real s2 = sxx + syy;
   Macro<Real> m;
   if (DEV) {
     m.drho = s0;
@@ -200,7 +206,8 @@ __host__ __device__ inline Real eq_dir(int i, const Macro<Real>& m, const EqCoef
 }
 
 // Same, for all directions at once using the +/- pairing: E(a) = C0 + a^2 (C2 + a^2 C4),
-// O(a) = a (C1 + a^2 C3), P(+-a) = E +- O. Writes out[i] = post-collision f + omega (eq - f).
+// O(a) = a (C1 + a^2 C3), P(+-a) = E +- O. Writes the post-collision value
+// f + omega (eq - f) = (1 - omega) f + omega eq, with omega folded into the weights.
 template <class S, class Real, bool DEV>
 __device__ inline void collide_bgk(Real (&p)[S::Q], const Macro<Real>& m,
                                    const Consts<Real>& c) {
@@ -214,11 +221,12 @@ __device__ inline void collide_bgk(Real (&p)[S::Q], const Macro<Real>& m,
     const Real C0m = k.k00m + c2 * (k.k01 + c2 * k.k02);
     const Real C1 = k.k10 + c2 * k.k11;
     const Real C2 = k.k20 + c2 * k.k21;
-    const Real wr = c.w[i0] * m.rho;          // w rho (all members of a shell share w)
-    const Real wd = c.w[i0] * m.drho;
+    const Real wr = om * c.w[i0] * m.rho;     // omega w rho (a shell shares w)
+    const Real wd = om * c.w[i0] * m.drho;
+    const Real keep = Real(1) - om;
     if (n == 1) {
       const Real eq = DEV ? (wr * C0m + wd) : (wr + wr * C0m);
-      p[i0] = p[i0] + om * (eq - p[i0]);
+      p[i0] = keep * p[i0] + eq;
       continue;
     }
 #pragma unroll
@@ -244,8 +252,8 @@ __device__ inline void collide_bgk(Real (&p)[S::Q], const Macro<Real>& m,
         eqp = base + odd;
         eqm = base - odd;
       }
-      p[ip] = p[ip] + om * (eqp - p[ip]);
-      p[im] = p[im] + om * (eqm - p[im]);
+      p[ip] = keep * p[ip] + eqp;
+      p[im] = keep * p[im] + eqm;
     }
   }
 }

@@ -5,119 +5,157 @@
 
 namespace lbm {
 
-// stage 1..4 of classical RK4 over one time step; fluid moments Ue frozen at time n. Targets,
-// stage values and all differences are FP64; the characteristic algebra runs in R.
-// One stage of classical RK4 for dU/dt of every edge-band node (fluid moments Ue frozen at
-// time n). Band node b -> edge (W, E, S, N), layer j = 1..M outward, tangential index t.
-// Rates: Eq. (thermal_LODI_macro_evo) with Eq. (PNR) for PNR-LODI edges, Eq.
-// (thermal_CBC_macro_evo) with Eq. (CBC-Relax) for CBC-relax edges; viscous part zero.
-// Derivatives per node index: normal one-sided 2nd order toward the outside, tangential
-// central (one-sided at the band ends); one node is r normalized lengths.
+// Rate dU/dt of one edge-band node (Sec. 4). U0: the node; U1, U2: the states one and two nodes
+// inward along the normal (band layers or fluid moments); Va, Vb, Vc: three consecutive nodes of
+// the same layer around it along the tangent with weights (ca, cb, cc) of the tangential
+// derivative. PNR-LODI: Eq. (PNR) with Eq. (thermal_LODI_macro_evo); CBC relax: Eq. (CBC-Relax)
+// with Eq. (thermal_CBC_macro_evo); viscous part zero. Differences in FP64, algebra in R.
 template <class R>
-__global__ void k_nrbc_stage(Geom g, BcParams bc, const double* __restrict__ Ue,
-                             double* __restrict__ V0, const double* __restrict__ Vin,
-                             double* __restrict__ Vout, double* __restrict__ acc, int stage) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= g.nb) return;
-  const int M = g.M, Lx = g.Lx, Ly = g.Ly;
-  int e, off, len, ueoff;
-  if (b < M * Ly) { e = 0; off = 0; len = Ly; ueoff = 0; }
-  else if (b < 2 * M * Ly) { e = 1; off = M * Ly; len = Ly; ueoff = 2 * Ly; }
-  else if (b < 2 * M * Ly + M * Lx) { e = 2; off = 2 * M * Ly; len = Lx; ueoff = 4 * Ly; }
-  else { e = 3; off = 2 * M * Ly + M * Lx; len = Lx; ueoff = 4 * Ly + 2 * Lx; }
-  const int loc = b - off;
-  const int j = loc / len + 1, t = loc - (j - 1) * len;
-  const bool xaxis = e < 2;
-  const double out = (e == 0 || e == 2) ? -1.0 : 1.0;
-  const int nb = g.nb, ne = g.ne;
-  auto node = [&](int jj, int tt) { return off + (jj - 1) * len + tt; };
-
-  const Prim U0d = load_prim(Vin, nb, b, xaxis);
-  const Prim U1 = j >= 2 ? load_prim(Vin, nb, node(j - 1, t), xaxis)
-                         : load_prim(Ue, ne, ueoff + t, xaxis);
-  const Prim U2 = j >= 3 ? load_prim(Vin, nb, node(j - 2, t), xaxis)
-                         : (j == 2 ? load_prim(Ue, ne, ueoff + t, xaxis)
-                                   : load_prim(Ue, ne, ueoff + len + t, xaxis));
-  // d/dx_axis per node = out * (3 U(x_b) - 4 U(x_b - n) + U(x_b - 2n)) / 2; differences in FP64
+__device__ inline void char_rate(const BcParams& bc, int variant, double out, const Prim& U0d,
+                                 const Prim& U1, const Prim& U2, const Prim& Va, const Prim& Vb,
+                                 const Prim& Vc, double ca, double cb, double cc, bool xaxis,
+                                 double kk[4]) {
   const double hs = 0.5 * out;
   PrimT<R> dn;
   dn.rho = R(hs * (3.0 * U0d.rho - 4.0 * U1.rho + U2.rho));
   dn.un = R(hs * (3.0 * U0d.un - 4.0 * U1.un + U2.un));
   dn.ut = R(hs * (3.0 * U0d.ut - 4.0 * U1.ut + U2.ut));
   dn.T = R(hs * (3.0 * U0d.T - 4.0 * U1.T + U2.T));
-
   const PrimT<R> U0 = to<R>(U0d);
-  const R inv_r = R(1.0 / bc.r);
+  const R inv_r = R(bc.inv_r);
   const R c = sqrt(R(2) * U0.T);  // gamma T with gamma = (D + 2) / D = 2
   const R lam[4] = {U0.un - c, U0.un, U0.un, U0.un + c};
   R wn[4];
   char_forward(U0, c, dn, wn);
   const R sgn = R(out);
   R tot[4];
-  if (bc.edge[e] == 0) {
-    // PNR-LODI: incoming amplitudes vanish, transverse terms dropped
+  if (variant == 0) {
     for (int k = 0; k < 4; ++k) tot[k] = (lam[k] * sgn < R(0)) ? R(0) : lam[k] * wn[k] * inv_r;
   } else {
-    // CBC relax: transverse amplitudes T = S B dU/dt_axis
-    const int ta = t == 0 ? 0 : (t == len - 1 ? t - 2 : t - 1);
-    const Prim Va = load_prim(Vin, nb, node(j, ta), xaxis);
-    const Prim Vb = load_prim(Vin, nb, node(j, ta + 1), xaxis);
-    const Prim Vc = load_prim(Vin, nb, node(j, ta + 2), xaxis);
-    double ca, cb, cc;
-    if (t == 0) { ca = -1.5; cb = 2.0; cc = -0.5; }
-    else if (t == len - 1) { ca = 0.5; cb = -2.0; cc = 1.5; }
-    else { ca = -0.5; cb = 0.0; cc = 0.5; }
     PrimT<R> dt;
     dt.rho = R(ca * Va.rho + cb * Vb.rho + cc * Vc.rho);
     dt.un = R(ca * Va.un + cb * Vb.un + cc * Vc.un);
     dt.ut = R(ca * Va.ut + cb * Vb.ut + cc * Vc.ut);
     dt.T = R(ca * Va.T + cb * Vb.T + cc * Vc.T);
-    // B dU along the tangential axis (tangential velocity u_t advects; P_t = T rho_t + rho T_t)
+    // B dU along the tangential axis (u_t advects; P_t = T rho_t + rho T_t; (2/D) T = T)
     PrimT<R> bd;
     bd.rho = U0.ut * dt.rho + U0.rho * dt.ut;
     bd.un = U0.ut * dt.un;
     bd.ut = (U0.T / U0.rho) * dt.rho + U0.ut * dt.ut + dt.T;
-    bd.T = U0.T * dt.ut + U0.ut * dt.T;  // (2/D) T with D = 2
+    bd.T = U0.T * dt.ut + U0.ut * dt.T;
     R Tc[4];
     char_forward(U0, c, bd, Tc);
-    const R relax = R((bc.relax_sign == 0.0 ? -1.0 : bc.relax_sign) * (1.0 - bc.beta));
+    const R relax = R(bc.relax_sign * (1.0 - bc.beta));
     for (int k = 0; k < 4; ++k) {
       const R Lbar = (lam[k] * sgn < R(0)) ? relax * Tc[k] : lam[k] * wn[k];
       tot[k] = (Lbar + Tc[k]) * inv_r;
     }
   }
   const PrimT<R> r = char_inverse(U0, c, tot);
-  // rate k = -S^-1 (...) in (rho, u_x, u_y, T)
-  const double k0 = -double(r.rho), k3 = -double(r.T);
-  const double kx = xaxis ? -double(r.un) : -double(r.ut), ky = xaxis ? -double(r.ut) : -double(r.un);
-  const double kk[4] = {k0, kx, ky, k3};
-  if (stage < 4) {
-    const double a = stage == 3 ? 1.0 : 0.5;
-    const double wgt = stage == 1 ? 1.0 : 2.0;
-    for (int q = 0; q < 4; ++q) {
-      Vout[q * nb + b] = V0[q * nb + b] + a * kk[q];
-      acc[q * nb + b] = (stage == 1 ? 0.0 : acc[q * nb + b]) + wgt * kk[q];
+  kk[0] = -double(r.rho);
+  kk[1] = xaxis ? -double(r.un) : -double(r.ut);
+  kk[2] = xaxis ? -double(r.ut) : -double(r.un);
+  kk[3] = -double(r.T);
+}
+
+// All four stages of classical RK4 for the targets of one chunk of one edge band, in shared
+// memory (fluid moments Ue frozen at time n). Block = one edge, tangential chunk [t0, t0 + T)
+// plus a 4-node halo on each side where the chunk does not end the band; thread = (layer,
+// position). Each stage shrinks the valid range by one node at a chunk cut, so the chunk's own
+// nodes see exactly the values a full-band evaluation would.
+constexpr int kChunk = 96, kHalo = 4, kText = kChunk + 2 * kHalo;
+
+template <class R>
+__global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
+                           double* __restrict__ Vg) {
+  const int M = g.M, Lx = g.Lx, Ly = g.Ly;
+  const int cw = (Ly + kChunk - 1) / kChunk, cs = (Lx + kChunk - 1) / kChunk;
+  int e, k = blockIdx.x;
+  if (k < cw) e = 0;
+  else if (k < 2 * cw) { e = 1; k -= cw; }
+  else if (k < 2 * cw + cs) { e = 2; k -= 2 * cw; }
+  else { e = 3; k -= 2 * cw + cs; }
+  const int len = e < 2 ? Ly : Lx;
+  const int off = e == 0 ? 0 : e == 1 ? M * Ly : e == 2 ? 2 * M * Ly : 2 * M * Ly + M * Lx;
+  const int ueoff = e == 0 ? 0 : e == 1 ? 2 * Ly : e == 2 ? 4 * Ly : 4 * Ly + 2 * Lx;
+  const bool xaxis = e < 2;
+  const double out = (e == 0 || e == 2) ? -1.0 : 1.0;
+  const int t0 = k * kChunk;
+  const int lo = max(0, t0 - kHalo), hi = min(len, t0 + kChunk + kHalo);
+  // shared state: [4 buffers][4 comps][M][kText] : V0, stage a, stage b, accumulator
+  extern __shared__ double sm[];
+  const int plane = M * kText;
+  auto at = [&](int buf, int q, int j, int t) -> double& {
+    return sm[(buf * 4 + q) * plane + (j - 1) * kText + (t - lo)];
+  };
+  const int tid = threadIdx.x;
+  const int j = tid / kText + 1, t = lo + tid % kText;
+  const bool live = j <= M && t < hi;
+  if (live)
+    for (int q = 0; q < 4; ++q) at(0, q, j, t) = Vg[q * g.nb + off + (j - 1) * len + t];
+  __syncthreads();
+  auto prim = [&](int buf, int jj, int tt) {
+    Prim u;
+    u.rho = at(buf, 0, jj, tt);
+    const double ux = at(buf, 1, jj, tt), uy = at(buf, 2, jj, tt);
+    u.un = xaxis ? ux : uy;
+    u.ut = xaxis ? uy : ux;
+    u.T = at(buf, 3, jj, tt);
+    return u;
+  };
+  auto fluid = [&](int layer, int tt) { return load_prim(Ue, g.ne, ueoff + layer * len + tt, xaxis); };
+  const int variant = bc.edge[e];
+  double kk[4] = {0, 0, 0, 0};
+  for (int s = 1; s <= 4; ++s) {
+    const int in_buf = s == 1 ? 0 : (s == 3 ? 2 : 1);  // V0, a, b, a
+    const int slo = lo == 0 ? 0 : lo + s, shi = hi == len ? len : hi - s;
+    if (live && t >= slo && t < shi) {
+      const Prim U0 = prim(in_buf, j, t);
+      const Prim U1 = j >= 2 ? prim(in_buf, j - 1, t) : fluid(0, t);
+      const Prim U2 = j >= 3 ? prim(in_buf, j - 2, t) : (j == 2 ? fluid(0, t) : fluid(1, t));
+      int ta;
+      double ca, cb, cc;
+      if (t == 0) { ta = 0; ca = -1.5; cb = 2.0; cc = -0.5; }
+      else if (t == len - 1) { ta = t - 2; ca = 0.5; cb = -2.0; cc = 1.5; }
+      else { ta = t - 1; ca = -0.5; cb = 0.0; cc = 0.5; }
+      Prim Va = U0, Vb = U0, Vc = U0;
+      if (variant != 0) {
+        Va = prim(in_buf, j, ta);
+        Vb = prim(in_buf, j, ta + 1);
+        Vc = prim(in_buf, j, ta + 2);
+      }
+      char_rate<R>(bc, variant, out, U0, U1, U2, Va, Vb, Vc, ca, cb, cc, xaxis, kk);
     }
-  } else {
-    for (int q = 0; q < 4; ++q) V0[q * nb + b] = V0[q * nb + b] + (acc[q * nb + b] + kk[q]) / 6.0;
+    __syncthreads();   // everyone has read the stage input before it is overwritten
+    if (live && t >= slo && t < shi) {
+      if (s < 4) {
+        const int out_buf = s == 2 ? 2 : 1;            // a, b, a
+        const double a = s == 3 ? 1.0 : 0.5, wgt = s == 1 ? 1.0 : 2.0;
+        for (int q = 0; q < 4; ++q) {
+          at(out_buf, q, j, t) = at(0, q, j, t) + a * kk[q];
+          at(3, q, j, t) = (s == 1 ? 0.0 : at(3, q, j, t)) + wgt * kk[q];
+        }
+      } else if (t >= t0 && t < t0 + kChunk) {
+        const double sixth = 1.0 / 6.0;
+        for (int q = 0; q < 4; ++q)
+          Vg[q * g.nb + off + (j - 1) * len + t] = at(0, q, j, t) + (at(3, q, j, t) + kk[q]) * sixth;
+      }
+    }
+    __syncthreads();
   }
 }
 
-// The four RK4 stages of one step (buffers: stage input Vtgt -> Va -> Vb -> Va; Vtgt updated in
-// place by the last stage).
+// The four RK4 stages of one step in one launch; fp32 selects FP32 characteristic algebra
+// (targets and differences stay FP64).
 cudaError_t launch_nrbc_stages(const Dev& d, bool fp32, cudaStream_t s) {
   const Geom& g = d.g;
-  const int nbk = (g.nb + 127) / 128;
-  const double* Vin[4] = {d.Vtgt, d.Va, d.Vb, d.Va};
-  double* Vout[4] = {d.Va, d.Vb, d.Va, nullptr};
-  for (int k = 1; k <= 4; ++k) {
-    if (fp32)
-      k_nrbc_stage<float><<<nbk, 128, 0, s>>>(g, d.bc, d.Uedge, d.Vtgt, Vin[k - 1], Vout[k - 1],
-                                               d.Vacc, k);
-    else
-      k_nrbc_stage<double><<<nbk, 128, 0, s>>>(g, d.bc, d.Uedge, d.Vtgt, Vin[k - 1], Vout[k - 1],
-                                                d.Vacc, k);
-  }
+  const int blocks = 2 * ((g.Ly + kChunk - 1) / kChunk) + 2 * ((g.Lx + kChunk - 1) / kChunk);
+  const int threads = (g.M * kText + 31) / 32 * 32;
+  const size_t smem = sizeof(double) * 16 * g.M * kText;
+  if (fp32)
+    k_nrbc_rk4<float><<<blocks, threads, smem, s>>>(g, d.bc, d.Uedge, d.Vtgt);
+  else
+    k_nrbc_rk4<double><<<blocks, threads, smem, s>>>(g, d.bc, d.Uedge, d.Vtgt);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "pml_fused.cuh"
 
 namespace lbm {
 
@@ -191,12 +192,31 @@ struct Ops {
     if (STREAM && d.bc.bc == 2) launch_nrbc_stages(d, sizeof(Real) == 4, bs);
     mark(1, bs);
     mark(4, bs);
-    k_frame1<S, Real, DEV, STREAM><<<(g.frame_n + 127) / 128, 128, 0, bs>>>(
-        g, c, A, B, static_cast<const Real*>(d.Sold), static_cast<Real*>(d.Snew), d.Uedge,
-        d.bc.bc == 2 ? 1 : 0, d.flag);
+    bool fused = false;
+    if constexpr (DEV) {
+      if (g.W > 0) {
+        // FP32: single-pass frame (tile + halo in shared memory)
+        const FrameTiles ft = make_frame_tiles(g, 256);
+        const size_t smem = pml_fused_smem<S>(ft);
+        static bool attr_set = false;
+        if (!attr_set) {
+          cudaFuncSetAttribute(k_pml_fused<S, STREAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024);
+          attr_set = true;
+        }
+        k_pml_fused<S, STREAM><<<ft.n_tb + ft.n_side, 256, smem, bs>>>(
+            g, c, ft, A, B, static_cast<const float*>(d.Sold), static_cast<float*>(d.Snew),
+            d.Uedge, d.bc.bc == 2 ? 1 : 0, d.flag);
+        fused = true;
+      }
+    }
+    if (!fused)
+      k_frame1<S, Real, DEV, STREAM><<<(g.frame_n + 127) / 128, 128, 0, bs>>>(
+          g, c, A, B, static_cast<const Real*>(d.Sold), static_cast<Real*>(d.Snew), d.Uedge,
+          d.bc.bc == 2 ? 1 : 0, d.flag);
     mark(5, bs);
     mark(6, bs);
-    if (g.W > 0)
+    if (g.W > 0 && !fused)
       k_frame2<S, Real><<<(g.frame_n + 127) / 128, 128, 0, bs>>>(
           g, c, B, static_cast<const Real*>(d.Sold), static_cast<const Real*>(d.Snew));
     mark(7, bs);

@@ -1,0 +1,175 @@
+// Single-pass PML frame kernel (FP32 deviation storage): one block per tile of the frame
+// (P + inner ring, distance < Wf from the edge of F) with a 2-node halo.
+//
+//  A  every node of tile + halo that carries Q (distance <= W) pulls its populations, takes
+//     its moments and stores Q_i = S_i^(n-1) + f_hat_i^n / 2 for all i in shared memory
+//     (trapezoidal accumulator, Eq. PMLQ; f_hat = f_eq - f_eq_bar, Eq. decomp-NJ);
+//  C  every owned node pulls again (cache hits), collides with BGK (equilibrium and moments
+//     kept from A), adds on P the PML term of Eq. (PMLCOLL) with grad Q from shared memory
+//     (Eq. FD-dx-center; Eq. FD-dx-bw along the outward normal on the outermost layer; the
+//     2-node halo covers both), writes the post-collision populations and
+//     S^n = S^(n-1) + f_hat^n.
+//
+// Tiles: the bottom and top bands (Wf rows, full width) use 32-wide tiles whose height splits
+// Wf evenly; the left and right bands (Wf columns) use tiles whose width splits Wf evenly.
+#pragma once
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+struct FrameTiles {
+  int tb_h, tb_rows, tb_cols;   // top / bottom bands: tile 32 x tb_h
+  int s_w, s_cols, s_h, s_rows; // left / right bands: tile s_w x s_h
+  int n_tb, n_side;             // tile counts (both bands of each kind)
+  int ext_max;                  // largest (w + 4) (h + 4)
+};
+
+inline FrameTiles make_frame_tiles(const Geom& g, int threads) {
+  FrameTiles t{};
+  const int Wf = g.Wf;
+  t.tb_rows = (Wf + 7) / 8;
+  t.tb_h = (Wf + t.tb_rows - 1) / t.tb_rows;
+  t.tb_cols = (g.Lx + 31) / 32;
+  t.s_cols = (Wf + 31) / 32;
+  t.s_w = (Wf + t.s_cols - 1) / t.s_cols;
+  t.s_h = threads / t.s_w;
+  if (t.s_h > 32) t.s_h = 32;
+  t.s_rows = (g.Ly - 2 * Wf + t.s_h - 1) / t.s_h;
+  t.n_tb = 2 * t.tb_rows * t.tb_cols;
+  t.n_side = 2 * t.s_cols * t.s_rows;
+  const int e1 = (32 + 4) * (t.tb_h + 4), e2 = (t.s_w + 4) * (t.s_h + 4);
+  t.ext_max = e1 > e2 ? e1 : e2;
+  return t;
+}
+
+// shared memory of k_pml_fused: Q on the extended tile, equilibria and moments of owned nodes
+template <class S>
+inline size_t pml_fused_smem(const FrameTiles& ft) {
+  return sizeof(float) * ((size_t)S::Q * ft.ext_max + (size_t)S::Q * 256 + 7 * 256);
+}
+
+template <class S, bool STREAM>
+__global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, FrameTiles ft,
+                                                   const float* __restrict__ A,
+                                                   float* __restrict__ B,
+                                                   const float* __restrict__ Sold,
+                                                   float* __restrict__ Snew, double* Uedge,
+                                                   int save_edges, int* flag) {
+  extern __shared__ float smem[];
+  // ---- tile of this block
+  int x0, y0, tw, th, band;  // band 0 bottom, 1 top, 2 left, 3 right
+  {
+    int k = blockIdx.x;
+    if (k < ft.n_tb) {
+      const int per = ft.tb_rows * ft.tb_cols;
+      band = k < per ? 0 : 1;
+      k -= band * per;
+      const int r = k / ft.tb_cols, cc = k - r * ft.tb_cols;
+      tw = 32;
+      th = ft.tb_h;
+      x0 = cc * 32;
+      y0 = band == 0 ? r * th : g.Ly - g.Wf + r * th;
+    } else {
+      k -= ft.n_tb;
+      const int per = ft.s_cols * ft.s_rows;
+      band = k < per ? 2 : 3;
+      k -= (band - 2) * per;
+      const int r = k / ft.s_cols, cc = k - r * ft.s_cols;
+      tw = ft.s_w;
+      th = ft.s_h;
+      x0 = band == 2 ? cc * tw : g.Lx - g.Wf + cc * tw;
+      y0 = g.Wf + r * th;
+    }
+  }
+  const int ew = tw + 4, eh = th + 4, next = ew * eh;
+  const int nown = tw * th;
+  float* Qs = smem;                       // [Q][next]   Q = S^(n-1) + f_hat / 2
+  float* Eq = Qs + S::Q * ft.ext_max;     // [Q][256]    f_eq of the owned nodes
+  float* Mc = Eq + S::Q * 256;            // [7][256]    moments of the owned nodes
+  const int tid = threadIdx.x;
+
+  // ---- A: Q on tile + halo; equilibria and moments of the owned nodes kept for phase C
+  for (int e = tid; e < next; e += blockDim.x) {
+    const int ex = e % ew, ey = e / ew;
+    const int x = x0 - 2 + ex, y = y0 - 2 + ey;
+    if (x < 0 || y < 0 || x >= g.Lx || y >= g.Ly || dist_out(g, x, y) > g.W) continue;
+    float p[S::Q];
+    load_pop<S, float, STREAM>(p, A, g, gindex(g, x, y));
+    const Macro<float> m = moments<S, float, true>(p, c);
+    const EqCoef<float> kc = eq_coef<S::ORDER, float>(m);
+    const int fi = frame_index(g, x, y);
+    const int tx = ex - 2, ty = ey - 2;
+    const int own = (tx >= 0 && ty >= 0 && tx < tw && ty < th) ? ty * tw + tx : -1;
+    if (own >= 0) {
+      Mc[0 * 256 + own] = m.rho;
+      Mc[1 * 256 + own] = m.drho;
+      Mc[2 * 256 + own] = m.inv_rho;
+      Mc[3 * 256 + own] = m.urx;
+      Mc[4 * 256 + own] = m.ury;
+      Mc[5 * 256 + own] = m.u2;
+      Mc[6 * 256 + own] = m.theta;
+    }
+#pragma unroll
+    for (int i = 0; i < S::Q; ++i) {
+      const float eq = eq_dir<S, float, true>(i, m, kc, c);
+      if (own >= 0) Eq[i * 256 + own] = eq;
+      Qs[i * next + e] = __ldg(Sold + (long long)i * g.Sp + fi) + 0.5f * (eq - c.eqbar[i]);
+    }
+  }
+  __syncthreads();
+
+  // ---- C: owned nodes
+  if (tid >= nown) return;
+  const int tx = tid % tw, ty = tid / tw;
+  const int x = x0 + tx, y = y0 + ty;
+  if (x >= g.Lx || y >= g.Ly) return;
+  bool owned;
+  if (band == 0) owned = y < g.Wf;
+  else if (band == 1) owned = y >= g.Ly - g.Wf;
+  else if (band == 2) owned = x < g.Wf && y < g.Ly - g.Wf;
+  else owned = y < g.Ly - g.Wf;
+  if (!owned) return;
+  const int d = dist_out(g, x, y);
+  const long long idx = gindex(g, x, y);
+  float p[S::Q];
+  load_pop<S, float, STREAM>(p, A, g, idx);
+  Macro<float> m;
+  m.rho = Mc[0 * 256 + tid];
+  m.drho = Mc[1 * 256 + tid];
+  m.inv_rho = Mc[2 * 256 + tid];
+  m.urx = Mc[3 * 256 + tid];
+  m.ury = Mc[4 * 256 + tid];
+  m.u2 = Mc[5 * 256 + tid];
+  m.theta = Mc[6 * 256 + tid];
+  if (unphysical(m)) *flag = 1;
+  if (save_edges && d < 2) save_edge_moments(g, Uedge, x, y, m, c.r);
+  const int fi = frame_index(g, x, y);
+  const int e0 = (ty + 2) * ew + (tx + 2);
+  const bool in_p = d < g.W;
+  const float sig = in_p ? sigma_at(c, g.W, d) : 0.f;
+  // gradient stencils on the shared-memory tile (offsets in extended-tile units)
+  float cx0 = 0.5f, cx1 = -0.5f, cx2 = 0.f, cy0 = 0.5f, cy1 = -0.5f, cy2 = 0.f;
+  int ox0 = 1, ox1 = -1, ox2 = 0, oy0 = ew, oy1 = -ew, oy2 = 0;
+  if (x == 0) { cx0 = -1.5f; cx1 = 2.f; cx2 = -0.5f; ox0 = 0; ox1 = 1; ox2 = 2; }
+  else if (x == g.Lx - 1) { cx0 = 1.5f; cx1 = -2.f; cx2 = 0.5f; ox0 = 0; ox1 = -1; ox2 = -2; }
+  if (y == 0) { cy0 = -1.5f; cy1 = 2.f; cy2 = -0.5f; oy0 = 0; oy1 = ew; oy2 = 2 * ew; }
+  else if (y == g.Ly - 1) { cy0 = 1.5f; cy1 = -2.f; cy2 = 0.5f; oy0 = 0; oy1 = -ew; oy2 = -2 * ew; }
+#pragma unroll
+  for (int i = 0; i < S::Q; ++i) {
+    const float eq = Eq[i * 256 + tid];
+    const float fhat = eq - c.eqbar[i];
+    const float* q = Qs + i * next + e0;
+    const float qn = q[0];
+    Snew[(long long)i * g.Sp + fi] = __ldg(Sold + (long long)i * g.Sp + fi) + fhat;  // S^n
+    float out = p[i] + c.omega * (eq - p[i]);
+    if (in_p) {
+      float gq = 0.f;
+      if (S::ex(i) != 0) gq += float(S::ex(i)) * (cx0 * q[ox0] + cx1 * q[ox1] + cx2 * q[ox2]);
+      if (S::ey(i) != 0) gq += float(S::ey(i)) * (cy0 * q[oy0] + cy1 * q[oy1] + cy2 * q[oy2]);
+      out = out - sig * (gq + 2.f * fhat + sig * qn);
+    }
+    B[(long long)i * g.plane + idx] = out;
+  }
+}
+
+}  // namespace lbm

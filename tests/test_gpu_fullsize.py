@@ -1,0 +1,65 @@
+"""Parity at the benchmark's full size (2048^2 bulk + PML 32, characteristic BC, D2Q37), in the
+launch configuration bench.py times (lbm_step replaying the step graph).
+
+1. Sampled interior nodes: after n steps a node farther than 4n from the PML depends only on
+   initial data within 3n nodes, so the oracle run on a small periodic window of the initial
+   fields around the node reproduces it; compared node by node (FP64 1e-12, FP32 1e-5).
+2. Properties that hold at any size: a centred pulse with no mean flow and PNR-LODI on every
+   edge stays mirror- and transpose-symmetric through the PML and boundary kernels.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import OracleLBM
+from parity_helpers import case_kwargs, make_solver
+
+pytestmark = pytest.mark.gpu
+
+N, W, STEPS = 2048, 32, 4
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32dev", 1e-5)])
+def test_sampled_interior_nodes_match_oracle_windows(precision, tol):
+    c = wl.vortex_2048()
+    fields = c.fields()
+    kw = case_kwargs(nx=c.nx, ny=c.ny, W=c.W, tau=c.tau, sigma_max=c.sigma_max,
+                     sigma_power=c.sigma_power, bc=c.bc, nrbc_edges=c.nrbc_edges, beta=c.beta,
+                     mean=c.mean)
+    with make_solver(kw, precision) as s:
+        s.init(*fields)
+        s.step(STEPS)
+        got = s.moments()
+    rng = np.random.default_rng(7)
+    L = c.nx + 2 * c.W
+    lo = c.W + 4 * STEPS + 1
+    R = 3 * STEPS + 2
+    # half of the samples inside the vortex core, half anywhere in the far interior
+    centre = (L - 1) / 2.0
+    pts = [(int(centre + dx), int(centre + dy)) for dx, dy in rng.integers(-30, 30, size=(8, 2))]
+    pts += [tuple(p) for p in rng.integers(lo, L - lo, size=(8, 2))]
+    worst = 0.0
+    for (x, y) in pts:
+        win = tuple(f[y - R:y + R + 1, x - R:x + R + 1] for f in fields)
+        o = OracleLBM(2 * R + 1, 2 * R + 1, 0, c.tau, bc="periodic")
+        o.init(*win)
+        o.step(STEPS)
+        ref = [f[R, R] for f in o.fields()]
+        err = [abs(got[0][y, x] - ref[0]) / ref[0], abs(got[1][y, x] - ref[1]),
+               abs(got[2][y, x] - ref[2]), abs(got[3][y, x] - ref[3]) / ref[3]]
+        worst = max(worst, max(err))
+    print(precision, "worst sampled error", worst)
+    assert worst < tol
+
+
+def test_full_size_symmetry_through_pml_and_boundary():
+    kw = case_kwargs(nx=N, ny=N, W=W, tau=0.8, sigma_max=0.1, sigma_power=3, bc="nrbc",
+                     nrbc_edges=(0, 0, 0, 0))
+    with make_solver(kw, "fp64") as s:
+        s.init(*wl.pressure_pulse(N, N, W, amp=1e-3, halfwidth=600.0))
+        s.step(40)
+        rho = s.moments()[0] - 1.0
+    assert np.abs(rho[:W + 2, :]).max() > 1e-9        # the pulse reaches the PML
+    assert np.max(np.abs(rho - rho[:, ::-1])) < 1e-13
+    assert np.max(np.abs(rho - rho[::-1, :])) < 1e-13
+    assert np.max(np.abs(rho - rho.T)) < 1e-13
