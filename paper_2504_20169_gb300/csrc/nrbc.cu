@@ -63,7 +63,7 @@ __device__ inline void char_rate(const BcParams& bc, int variant, double out, co
 // plus a 4-node halo on each side where the chunk does not end the band; thread = (layer,
 // position). Each stage shrinks the valid range by one node at a chunk cut, so the chunk's own
 // nodes see exactly the values a full-band evaluation would.
-constexpr int kChunk = 96, kHalo = 4, kText = kChunk + 2 * kHalo;
+constexpr int kChunk = 32, kHalo = 4, kText = kChunk + 2 * kHalo;
 
 template <class R>
 __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,

@@ -4,8 +4,8 @@
 //  A  every node of tile + halo that carries Q (distance <= W) pulls its populations, takes
 //     its moments and stores Q_i = S_i^(n-1) + f_hat_i^n / 2 for all i in shared memory
 //     (trapezoidal accumulator, Eq. PMLQ; f_hat = f_eq - f_eq_bar, Eq. decomp-NJ);
-//  C  every owned node pulls again (cache hits), collides with BGK (equilibrium and moments
-//     kept from A), adds on P the PML term of Eq. (PMLCOLL) with grad Q from shared memory
+//  C  every owned node pulls again (cache hits), collides with BGK (moments kept from A),
+//     adds on P the PML term of Eq. (PMLCOLL) with grad Q from shared memory
 //     (Eq. FD-dx-center; Eq. FD-dx-bw along the outward normal on the outermost layer; the
 //     2-node halo covers both), writes the post-collision populations and
 //     S^n = S^(n-1) + f_hat^n.
@@ -42,10 +42,10 @@ inline FrameTiles make_frame_tiles(const Geom& g, int threads) {
   return t;
 }
 
-// shared memory of k_pml_fused: Q on the extended tile, equilibria and moments of owned nodes
+// shared memory of k_pml_fused: Q on the extended tile and the moments of the owned nodes
 template <class S>
 inline size_t pml_fused_smem(const FrameTiles& ft) {
-  return sizeof(float) * ((size_t)S::Q * ft.ext_max + (size_t)S::Q * 256 + 7 * 256);
+  return sizeof(float) * ((size_t)S::Q * ft.ext_max + 7 * 256);
 }
 
 template <class S, bool STREAM>
@@ -84,8 +84,7 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   const int ew = tw + 4, eh = th + 4, next = ew * eh;
   const int nown = tw * th;
   float* Qs = smem;                       // [Q][next]   Q = S^(n-1) + f_hat / 2
-  float* Eq = Qs + S::Q * ft.ext_max;     // [Q][256]    f_eq of the owned nodes
-  float* Mc = Eq + S::Q * 256;            // [7][256]    moments of the owned nodes
+  float* Mc = Qs + S::Q * ft.ext_max;     // [7][256]    moments of the owned nodes
   const int tid = threadIdx.x;
 
   // ---- A: Q on tile + halo; equilibria and moments of the owned nodes kept for phase C
@@ -112,7 +111,6 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       const float eq = eq_dir<S, float, true>(i, m, kc, c);
-      if (own >= 0) Eq[i * 256 + own] = eq;
       Qs[i * next + e] = __ldg(Sold + (long long)i * g.Sp + fi) + 0.5f * (eq - c.eqbar[i]);
     }
   }
@@ -143,6 +141,7 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   m.theta = Mc[6 * 256 + tid];
   if (unphysical(m)) *flag = 1;
   if (save_edges && d < 2) save_edge_moments(g, Uedge, x, y, m, c.r);
+  const EqCoef<float> kc = eq_coef<S::ORDER, float>(m);
   const int fi = frame_index(g, x, y);
   const int e0 = (ty + 2) * ew + (tx + 2);
   const bool in_p = d < g.W;
@@ -156,7 +155,7 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   else if (y == g.Ly - 1) { cy0 = 1.5f; cy1 = -2.f; cy2 = 0.5f; oy0 = 0; oy1 = -ew; oy2 = -2 * ew; }
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) {
-    const float eq = Eq[i * 256 + tid];
+    const float eq = eq_dir<S, float, true>(i, m, kc, c);
     const float fhat = eq - c.eqbar[i];
     const float* q = Qs + i * next + e0;
     const float qn = q[0];
