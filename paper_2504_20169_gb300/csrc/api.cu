@@ -440,6 +440,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   d.cd.sigma_max = sg.sigma_max; d.cd.power = sg.power;
   d.cf.r = (float)ctx->r; d.cf.r2 = (float)(ctx->r * ctx->r); d.cf.omega = (float)ctx->omega;
   d.cf.sigma_max = (float)sg.sigma_max; d.cf.power = sg.power;
+  if (ctx->ops.prepare() != cudaSuccess) return oom("kernel attributes");
   if (cudaDeviceSynchronize() != cudaSuccess) return oom("device sync");
   *out = ctx;
   return LBM_OK;

@@ -37,6 +37,7 @@ struct Dev {
 constexpr int kKernelClasses = 5;
 
 struct OpsTable {
+  cudaError_t (*prepare)();   // kernel attributes on the current device
   cudaError_t (*step)(const Dev&, bool stream);
   cudaError_t (*init_eq)(const Dev&, const double*, const double*, const double*, const double*);
   cudaError_t (*fields)(const Dev&, const void* src, bool stream, int region, double* const o[4],

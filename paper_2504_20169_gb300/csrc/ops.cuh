@@ -198,12 +198,6 @@ struct Ops {
         // FP32: single-pass frame (tile + halo in shared memory)
         const FrameTiles ft = make_frame_tiles(g, 256);
         const size_t smem = pml_fused_smem<S>(ft);
-        static bool attr_set = false;
-        if (!attr_set) {
-          cudaFuncSetAttribute(k_pml_fused<S, STREAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               200 * 1024);
-          attr_set = true;
-        }
         k_pml_fused<S, STREAM><<<ft.n_tb + ft.n_side, 256, smem, bs>>>(
             g, c, ft, A, B, static_cast<const float*>(d.Sold), static_cast<float*>(d.Snew),
             d.Uedge, d.bc.bc == 2 ? 1 : 0, d.flag);
@@ -280,8 +274,22 @@ struct Ops {
     return cudaGetLastError();
   }
 
+  // per-device kernel attributes, set once for every context on the context's device
+  static cudaError_t prepare() {
+    if constexpr (DEV) {
+      cudaError_t e = cudaFuncSetAttribute(k_pml_fused<S, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pml_fused<S, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      return e;
+    }
+    return cudaSuccess;
+  }
+
   static OpsTable table() {
     OpsTable t;
+    t.prepare = &prepare;
     t.step = &step;
     t.init_eq = &init_eq;
     t.fields = &fields;

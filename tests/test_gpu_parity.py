@@ -98,20 +98,37 @@ def test_parity_periodic_ragged():
     check(kw, fields, 100)
 
 
-@pytest.mark.parametrize("nx,ny,W", [(45, 37, 5), (33, 70, 2), (96, 40, 35)])
-def test_parity_ragged_pml_sizes(nx, ny, W):
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+@pytest.mark.parametrize("nx,ny,W", [(45, 37, 5), (33, 70, 2), (96, 40, 35), (200, 9, 64)])
+def test_parity_ragged_pml_sizes(nx, ny, W, precision):
+    """Ragged bulk sizes and PML widths from 2 to 64: partial interior tiles, frame tiles of odd
+    shapes (the FP32 frame kernel sizes its tiles from the frame depth), short edge bands."""
     kw = case_kwargs(nx=nx, ny=ny, W=W, tau=0.75, sigma_max=0.2, sigma_power=2, bc="zg")
     fields = wl.random_smooth_state(nx, ny, W, seed=nx + ny, du=0.05)
-    check(kw, fields, 30)
+    check(kw, fields, 30, precision)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+@pytest.mark.parametrize("nx,ny,W,steps", [(16, 12, 2, 15), (150, 20, 3, 25), (20, 300, 40, 25)])
+def test_parity_nrbc_band_lengths(nx, ny, W, steps, precision):
+    """Characteristic targets on bands shorter and longer than one RK4 chunk (32 nodes + halo),
+    with CBC relax on every edge so the tangential stencil crosses chunk cuts. (An 8 x 8 bulk
+    with CBC relax on every edge diverges in the oracle itself within 25 steps.)"""
+    kw = case_kwargs(nx=nx, ny=ny, W=W, tau=0.7, sigma_max=0.05, sigma_power=3, bc="nrbc",
+                     nrbc_edges=(1, 1, 1, 1), beta=0.3, mean=(1.0, 0.1, 0.05, 1.0))
+    fields = wl.random_smooth_state(nx, ny, W, seed=3 * nx + ny, du=0.03,
+                                    mean_u=(0.1, 0.05))
+    check(kw, fields, steps, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
 @pytest.mark.parametrize("q", [17, 9])
 @pytest.mark.parametrize("bc", ["zg", "nrbc"])
-def test_parity_other_stencils(q, bc):
+def test_parity_other_stencils(q, bc, precision):
     kw = case_kwargs(nx=36, ny=30, W=4, tau=0.7, sigma_max=0.1, bc=bc, q=q,
                      nrbc_edges=(0, 1, 0, 1), beta=0.2, mean=(1.0, 0.05, 0.0, 1.0))
     fields = wl.pressure_pulse(36, 30, 4, amp=1e-3, halfwidth=3.0, u0=(0.05, 0.0))
-    check(kw, fields, 50)
+    check(kw, fields, 50, precision)
 
 
 def test_totals_and_error_sums_match_oracle():
