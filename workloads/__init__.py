@@ -95,6 +95,26 @@ def density_step(Lx, Ly, Ma=0.05, rho0=1.0, rho1=1.05, s=0.5, W=0):
     return rho, np.full_like(rho, Ma), np.zeros_like(rho), np.ones_like(rho)
 
 
+def paper_vortex(nx, ny, W, Ma=0.1, b=0.2, rstar=0.5, K=180.0, rho0=1.0, T0=1.0, pad=0):
+    """Sec. 5.2 thermal vortex on an nx x ny bulk: normalized coordinates
+    x* = 2(x - 1)/(nx - 1) - 1 (x counted from 1 over the bulk), centre (K/(nx - 1), 0); inside
+    radius r*: u = u0 + (5/2) u0 2^(-(x^2 + y^2)/b^2) (y, -x), T = T0 + y (5/2) u0 2^(...),
+    rho = rho0; u0 = Ma (c_s = 1). The paper does not give b, r*, K: b = 0.2, r* = 0.5, K = 180
+    are this build's choice. `pad` extends the grid by pad nodes per side with the same formula
+    (periodic reference runs), on top of the W PML layers."""
+    Ly, Lx = ny + 2 * (W + pad), nx + 2 * (W + pad)
+    y, x = np.meshgrid(np.arange(Ly, dtype=np.float64) - (W + pad) + 1.0,
+                       np.arange(Lx, dtype=np.float64) - (W + pad) + 1.0, indexing="ij")
+    xs = 2.0 * (x - 1.0) / (nx - 1.0) - 1.0 - K / (nx - 1.0)
+    ys = 2.0 * (y - 1.0) / (ny - 1.0) - 1.0
+    inside = xs * xs + ys * ys < rstar * rstar
+    g = 2.5 * Ma * np.power(2.0, -(xs * xs + ys * ys) / (b * b))
+    ux = Ma + np.where(inside, g * ys, 0.0)
+    uy = np.where(inside, -g * xs, 0.0)
+    T = T0 + np.where(inside, ys * g, 0.0)
+    return np.full_like(ux, rho0), ux, uy, T
+
+
 def random_smooth_state(nx, ny, W, seed, du=0.05, drho=0.02, dT=0.02, mean_u=(0.0, 0.0),
                         modes=4):
     """Seeded smooth random perturbation (sum of low Fourier modes) around a mean state."""
