@@ -63,3 +63,35 @@ def test_full_size_symmetry_through_pml_and_boundary():
     assert np.max(np.abs(rho - rho[:, ::-1])) < 1e-13
     assert np.max(np.abs(rho - rho[::-1, :])) < 1e-13
     assert np.max(np.abs(rho - rho.T)) < 1e-13
+
+
+def test_stress_8192_fp32_runs_and_matches_sampled_oracle_windows():
+    """The 8192^2 + PML 64 case (four seeded pulses in a Mach 0.2 flow, tau 0.52, NRBC): about
+    20 GB of FP32 populations; checks 64-bit indexing, finiteness over F and sampled interior
+    nodes after 3 steps against oracle windows."""
+    c = wl.stress_8192()
+    fields = c.fields()
+    kw = case_kwargs(nx=c.nx, ny=c.ny, W=c.W, tau=c.tau, sigma_max=c.sigma_max,
+                     sigma_power=c.sigma_power, bc=c.bc, nrbc_edges=c.nrbc_edges, beta=c.beta,
+                     mean=c.mean)
+    n = 3
+    with make_solver(kw, "fp32dev") as s:
+        s.init(*fields)
+        s.step(n)
+        got = s.moments()
+        tot = s.reduce()
+    assert tot[6] == 0 and all(np.isfinite(a).all() for a in got)
+    L = c.nx + 2 * c.W
+    R = 3 * n + 2
+    rng = np.random.default_rng(11)
+    lo = c.W + 4 * n + 1
+    worst = 0.0
+    for (x, y) in [tuple(p) for p in rng.integers(lo, L - lo, size=(12, 2))]:
+        win = tuple(f[y - R:y + R + 1, x - R:x + R + 1] for f in fields)
+        o = OracleLBM(2 * R + 1, 2 * R + 1, 0, c.tau, bc="periodic")
+        o.init(*win)
+        o.step(n)
+        ref = [f[R, R] for f in o.fields()]
+        worst = max(worst, abs(got[0][y, x] - ref[0]), abs(got[1][y, x] - ref[1]),
+                    abs(got[2][y, x] - ref[2]), abs(got[3][y, x] - ref[3]))
+    assert worst < 1e-5
