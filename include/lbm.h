@@ -70,7 +70,7 @@ typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1 } lbm_precision;
 typedef struct { int nx, ny; } lbm_grid;
 
 /* Eq. (PML_ramp): sigma = sigma_max (i / W)^power on PML layer i = 1..W (power 2 in the
- * paper). Corner layers use i = max(i_x, i_y). */
+ * paper). Corner layers use the larger layer fraction max(i_x / W_x, i_y / W_y). */
 typedef struct { double sigma_max; int power; } lbm_sigma_profile;
 
 typedef struct {
@@ -78,6 +78,11 @@ typedef struct {
   double beta;                  /* relaxation Mach number "Ma" of Eq. (CBC-Relax)            */
   double relax_sign;            /* -1 (default reading) or +1 (as printed); 0 means -1      */
   double rho0, u0x, u0y, T0;    /* mean state: f_eq_bar of the PML (Eq. decomp-NJ)          */
+  int pml_width_y;              /* PML layers on the S and N edges; negative: pml_width.    */
+                                /* (A zero-filled struct therefore has no PML on S and N.)  */
+  int periodic_y;               /* 1: the y axis is periodic (Sec. 5.1 setting): no S / N    */
+                                /* boundary, requires pml_width_y <= 0 and, with LBM_BC_NRBC, */
+                                /* PNR_LODI on the W and E edges                             */
 } lbm_bc_params;
 
 /* Create a context. tau > 1/2 (tau = +INFINITY gives collisionless free streaming);

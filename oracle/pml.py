@@ -26,29 +26,47 @@ from __future__ import annotations
 import numpy as np
 
 
-def layer_index(Lx: int, Ly: int, W: int) -> np.ndarray:
-    """(Ly, Lx) int array: PML layer index i in 1..W on P, 0 in the bulk."""
-    x = np.arange(Lx)
-    y = np.arange(Ly)
-    dx = np.maximum(0, np.maximum(W - x, x - (Lx - 1 - W)))
-    dy = np.maximum(0, np.maximum(W - y, y - (Ly - 1 - W)))
-    return np.maximum(dx[None, :], dy[:, None])
-
-
-def sigma_field(Lx, Ly, W, sigma_max, power):
-    """Eq. (PML_ramp): sigma = sigma_max (i / W)^p on P, 0 in the bulk."""
+def _axis_layers(L, W):
+    """PML layer index along one axis: W - (distance to the nearer end), 0 outside the PML."""
     if W == 0:
-        return np.zeros((Ly, Lx))
-    i = layer_index(Lx, Ly, W).astype(np.float64)
-    return np.where(i > 0, sigma_max * (i / W) ** power, 0.0)
+        return np.zeros(L, dtype=np.int64)
+    z = np.arange(L)
+    return np.maximum(0, np.maximum(W - z, z - (L - 1 - W)))
 
 
-def q_support(Lx, Ly, W) -> np.ndarray:
-    """Nodes where Q is kept: P plus the bulk ring adjacent to P."""
+def layer_index(Lx: int, Ly: int, W: int, Wy: int = None) -> np.ndarray:
+    """(Ly, Lx) int array: PML layer index i in 1..W on P, 0 in the bulk (equal widths)."""
+    Wy = W if Wy is None else Wy
+    return np.maximum(_axis_layers(Lx, W)[None, :], _axis_layers(Ly, Wy)[:, None])
+
+
+def sigma_field(Lx, Ly, W, sigma_max, power, Wy=None):
+    """Eq. (PML_ramp): sigma = sigma_max (i / W)^p on P, 0 in the bulk. With different widths
+    on the x edges (W) and y edges (Wy) the layer fraction is max(i_x / W, i_y / Wy)."""
+    Wy = W if Wy is None else Wy
+    fx = _axis_layers(Lx, W) / W if W > 0 else np.zeros(Lx)
+    fy = _axis_layers(Ly, Wy) / Wy if Wy > 0 else np.zeros(Ly)
+    frac = np.maximum(fx[None, :], fy[:, None])
+    return np.where(frac > 0, sigma_max * frac ** power, 0.0)
+
+
+def in_pml(Lx, Ly, W, Wy=None) -> np.ndarray:
+    """Nodes of P (PML layer index >= 1 along some axis)."""
+    Wy = W if Wy is None else Wy
+    return (_axis_layers(Lx, W)[None, :] > 0) | (_axis_layers(Ly, Wy)[:, None] > 0)
+
+
+def q_support(Lx, Ly, W, Wy=None) -> np.ndarray:
+    """Nodes where Q is kept: P plus the bulk nodes one step inside it along each PML axis (the
+    ring the central difference of the innermost layer reaches)."""
+    Wy = W if Wy is None else Wy
     x = np.arange(Lx)
     y = np.arange(Ly)
-    dist = np.minimum(np.minimum(x, Lx - 1 - x)[None, :], np.minimum(y, Ly - 1 - y)[:, None])
-    return dist <= W if W > 0 else np.zeros((Ly, Lx), dtype=bool)
+    dx = np.minimum(x, Lx - 1 - x)
+    dy = np.minimum(y, Ly - 1 - y)
+    sx = (dx <= W) if W > 0 else np.zeros(Lx, dtype=bool)
+    sy = (dy <= Wy) if Wy > 0 else np.zeros(Ly, dtype=bool)
+    return sx[None, :] | sy[:, None]
 
 
 def trapezoid_update(Q_prev, fhat_prev, fhat_now):
@@ -56,21 +74,25 @@ def trapezoid_update(Q_prev, fhat_prev, fhat_now):
     return Q_prev + 0.5 * (fhat_prev + fhat_now)
 
 
-def gradient(Q: np.ndarray):
+def gradient(Q: np.ndarray, periodic_y: bool = False):
     """Per-axis finite differences of Q (q, Ly, Lx) over F.
 
     Central differences Eq. (FD-dx-center) in the interior; at the outermost layer of F the
-    one-sided Eq. (FD-dx-bw) along the outward normal. Values are only used on P.
+    one-sided Eq. (FD-dx-bw) along the outward normal. Along a periodic y axis the central
+    difference wraps. Values are only used on P.
     """
     gx = np.zeros_like(Q)
     gy = np.zeros_like(Q)
     gx[:, :, 1:-1] = 0.5 * (Q[:, :, 2:] - Q[:, :, :-2])
-    gy[:, 1:-1, :] = 0.5 * (Q[:, 2:, :] - Q[:, :-2, :])
     # right edge: outward normal +x; left edge: outward normal -x
     gx[:, :, -1] = +0.5 * (3.0 * Q[:, :, -1] - 4.0 * Q[:, :, -2] + Q[:, :, -3])
     gx[:, :, 0] = -0.5 * (3.0 * Q[:, :, 0] - 4.0 * Q[:, :, 1] + Q[:, :, 2])
-    gy[:, -1, :] = +0.5 * (3.0 * Q[:, -1, :] - 4.0 * Q[:, -2, :] + Q[:, -3, :])
-    gy[:, 0, :] = -0.5 * (3.0 * Q[:, 0, :] - 4.0 * Q[:, 1, :] + Q[:, 2, :])
+    if periodic_y:
+        gy[:] = 0.5 * (np.roll(Q, -1, axis=1) - np.roll(Q, 1, axis=1))
+    else:
+        gy[:, 1:-1, :] = 0.5 * (Q[:, 2:, :] - Q[:, :-2, :])
+        gy[:, -1, :] = +0.5 * (3.0 * Q[:, -1, :] - 4.0 * Q[:, -2, :] + Q[:, -3, :])
+        gy[:, 0, :] = -0.5 * (3.0 * Q[:, 0, :] - 4.0 * Q[:, 1, :] + Q[:, 2, :])
     return gx, gy
 
 

@@ -40,11 +40,22 @@ EDGES = ("W", "E", "S", "N")
 class OracleLBM:
     def __init__(self, nx, ny, W, tau, sigma_max=0.0, sigma_power=2, bc="zg", q=37,
                  nrbc_edges=(0, 0, 0, 0), beta=0.0, mean=(1.0, 0.0, 0.0, 1.0),
-                 relax_sign=-1.0, pml_on=True):
+                 relax_sign=-1.0, pml_on=True, Wy=None, periodic_y=False):
+        """W: PML layers on the x edges (and on the y edges unless Wy is given). periodic_y:
+        the y axis wraps (no PML on it: Wy defaults to, and must be, 0); the x edges keep the
+        chosen BC."""
         self.lat = lattice(q)
         self.pml_on = pml_on
+        self.periodic_y = bool(periodic_y)
+        self.Wy = (0 if self.periodic_y else W) if Wy is None else Wy
+        if self.periodic_y and (self.Wy != 0 or bc == "periodic"):
+            raise ValueError("a periodic y axis has no PML (Wy = 0) and needs a zg/nrbc x edge")
+        if self.periodic_y and bc == "nrbc" and (nrbc_edges[0] or nrbc_edges[1]):
+            raise ValueError("CBC relax on an edge whose tangent is periodic is not supported")
+        if self.Wy == 1:
+            raise ValueError("a PML needs W >= 2 (one-sided difference reaches 2 nodes in)")
         self.nx, self.ny, self.W = nx, ny, W
-        self.Lx, self.Ly = nx + 2 * W, ny + 2 * W
+        self.Lx, self.Ly = nx + 2 * W, ny + 2 * self.Wy
         self.M = self.lat.M
         self.tau = tau
         self.bc = bc
@@ -57,9 +68,10 @@ class OracleLBM:
             raise ValueError("a PML needs W >= 2 (one-sided difference reaches 2 nodes in)")
         M, Lx, Ly = self.M, self.Lx, self.Ly
         self.Gx, self.Gy = Lx + 2 * M, Ly + 2 * M
-        self.sigma = pml.sigma_field(Lx, Ly, W, sigma_max, sigma_power)
-        self.in_P = pml.layer_index(Lx, Ly, W) > 0 if W > 0 else np.zeros((Ly, Lx), bool)
-        self.qsup = pml.q_support(Lx, Ly, W)
+        self.sigma = pml.sigma_field(Lx, Ly, W, sigma_max, sigma_power, self.Wy)
+        self.in_P = pml.in_pml(Lx, Ly, W, self.Wy)
+        self.qsup = pml.q_support(Lx, Ly, W, self.Wy)
+        self.edges = ("W", "E") if self.periodic_y else EDGES
         rho0, u0x, u0y, T0 = mean
         self.fbar = feq(np.float64(rho0), np.array([u0x, u0y]), np.float64(T0),
                         self.lat.xi, self.lat.w, self.lat.order)          # f_eq_bar (Eq. decomp-NJ)
@@ -104,6 +116,8 @@ class OracleLBM:
         f[:] = f[:, self._cly[:, None], self._clx[None, :]]
         if self.bc == "nrbc":
             for k, edge in enumerate(EDGES):
+                if edge not in self.edges:
+                    continue
                 for j in range(1, self.M + 1):
                     by, bx, fy, fx = self._edge_nodes(edge, j)
                     ff = f[:, fy, fx]
@@ -111,6 +125,10 @@ class OracleLBM:
                     Ut = self.Utgt[edge][j - 1]
                     f[:, by, bx] = (self._feq(Ut[:, 0], Ut[:, 1:3].T, Ut[:, 3])
                                     + ff - self._feq(rho, u, T))
+        if self.periodic_y:
+            # rows outside F along the periodic axis are images of rows inside, boundary
+            # columns included (those hold the x-edge boundary values just set)
+            f[:] = f[:, self._wry, :]
 
     def _target_rates(self, V, U):
         """dU/dt of every edge-band node for the boundary state V (dict edge -> M layers of
@@ -118,6 +136,8 @@ class OracleLBM:
         M = self.M
         rates = {}
         for k, edge in enumerate(EDGES):
+            if edge not in self.edges:
+                continue
             axis = 0 if edge in ("W", "E") else 1
             out = -1.0 if edge in ("W", "S") else 1.0
             layers = []
@@ -150,7 +170,7 @@ class OracleLBM:
         V0 = self.Utgt
 
         def axpy(a, K):
-            return {e: [v + a * kk for v, kk in zip(V0[e], K[e])] for e in EDGES}
+            return {e: [v + a * kk for v, kk in zip(V0[e], K[e])] for e in self.edges}
 
         k1 = self._target_rates(V0, U)
         k2 = self._target_rates(axpy(0.5, k1), U)
@@ -158,7 +178,7 @@ class OracleLBM:
         k4 = self._target_rates(axpy(1.0, k3), U)
         self.Utgt = {e: [v + (a + 2.0 * b + 2.0 * c + d) / 6.0
                          for v, a, b, c, d in zip(V0[e], k1[e], k2[e], k3[e], k4[e])]
-                     for e in EDGES}
+                     for e in self.edges}
 
     # ---------------------------------------------------------------- public
     def init(self, rho, ux, uy, T):
@@ -169,7 +189,7 @@ class OracleLBM:
         if self.bc == "nrbc":
             Uf = np.stack([rho, ux, uy, T], axis=-1)
             self.Utgt = {}
-            for edge in EDGES:
+            for edge in self.edges:
                 layers = []
                 for j in range(1, M + 1):
                     by, bx, fy, fx = self._edge_nodes(edge, j)
@@ -188,7 +208,7 @@ class OracleLBM:
             rho, u, T = moments(f, lat.xi)                                   # 1
             fe = self._feq(rho, u, T)                                        # 2
             fstar = bgk(f, fe, self.tau)                                     # 5 (BGK part)
-            if self.W > 0 and self.pml_on:
+            if (self.W > 0 or self.Wy > 0) and self.pml_on:
                 Fs = self.Fs
                 fhat = np.where(self.qsup, fe[Fs] - self.fbar[:, None, None], 0.0)   # 3
                 if self.Q is None:
@@ -197,9 +217,13 @@ class OracleLBM:
                     Q = np.where(self.qsup, pml.trapezoid_update(self.Q, self.fhat_prev, fhat),
                                  0.0)
                 self.Q, self.fhat_prev = Q, fhat
-                gx, gy = pml.gradient(Q)                                     # 4
+                gx, gy = pml.gradient(Q, self.periodic_y)                    # 4
                 om = pml.omega_pml(lat.e, gx, gy, fhat, Q, self.sigma)
                 fstar[Fs] = fstar[Fs] + np.where(self.in_P, om, 0.0)         # 5 (PML part)
+            if self.periodic_y:
+                # the rows beyond a periodic y axis carry the post-collision populations of
+                # the rows they image (PML term included), as on an unbounded periodic lattice
+                fstar[:] = fstar[:, self._wry, :]
             fnew = np.empty_like(f)                                          # 6
             M = self.M
             for i, (ex, ey) in enumerate(lat.e):
@@ -217,8 +241,8 @@ class OracleLBM:
         rho, u, T = moments(self.f[self.Fs], self.lat.xi)
         out = (rho, u[0], u[1], T)
         if region == "bulk":
-            W = self.W
-            out = tuple(a[W:W + self.ny, W:W + self.nx] for a in out)
+            W, Wy = self.W, self.Wy
+            out = tuple(a[Wy:Wy + self.ny, W:W + self.nx] for a in out)
         return out
 
     def totals(self):

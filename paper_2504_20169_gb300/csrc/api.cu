@@ -267,20 +267,23 @@ lbm_status lbm_lattice_info(lbm_stencil stencil, int* q, int* e, double* w, doub
 }
 
 // Storage geometry of a grid (section "Storage" of lbm_device.cuh) and the bytes it needs.
-static Geom make_geom(int nx, int ny, int W, int M) {
+static Geom make_geom(int nx, int ny, int W, int M, int Wy, int py) {
   Geom g{};
   g.nx = nx;
   g.ny = ny;
   g.W = W;
+  g.Wy = Wy;
+  g.py = py;
   g.M = M;
   g.Lx = nx + 2 * W;
-  g.Ly = ny + 2 * W;
+  g.Ly = ny + 2 * Wy;
   g.cF0 = 32;
   g.pitch = ((g.cF0 + g.Lx + g.M) + 31) / 32 * 32;
   g.plane = ((long long)g.pitch * (g.Ly + 2 * g.M) + 63) / 64 * 64;
   g.Wf = g.W > 0 ? std::max(g.W + 1, g.M) : g.M;
-  g.frame_n = 2 * g.Wf * g.Lx + 2 * (g.Ly - 2 * g.Wf) * g.Wf;
-  g.Sp = g.W > 0 ? ((long long)g.frame_n + 31) / 32 * 32 : 0;
+  g.Wfy = py ? 0 : (g.Wy > 0 ? std::max(g.Wy + 1, g.M) : g.M);
+  g.frame_n = 2 * g.Wfy * g.Lx + 2 * (g.Ly - 2 * g.Wfy) * g.Wf;
+  g.Sp = (g.W > 0 || g.Wy > 0) ? ((long long)g.frame_n + 31) / 32 * 32 : 0;
   g.nb = 2 * g.M * (g.Lx + g.Ly);
   g.ne = 4 * (g.Lx + g.Ly);
   g.ngamma = 2 * g.M * (g.Lx + 2 * g.M) + 2 * g.M * g.Ly;
@@ -302,7 +305,7 @@ extern "C" lbm_status lbm_estimate_bytes(const lbm_grid* grid, lbm_stencil stenc
       pml_width == 1 || (bc == LBM_BC_PERIODIC && pml_width != 0) ||
       (precision != LBM_FP64 && precision != LBM_FP32_DEV))
     return LBM_EINVAL;
-  const Geom g = make_geom(grid->nx, grid->ny, pml_width, halo_of(q));
+  const Geom g = make_geom(grid->nx, grid->ny, pml_width, halo_of(q), pml_width, 0);
   *bytes = bytes_of(g, q, precision == LBM_FP64 ? 8 : 4);
   return LBM_OK;
 }
@@ -327,7 +330,15 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
     return fail("bad sigma profile");
   lbm_bc_params bp;
   if (bcp) bp = *bcp;
-  else { std::memset(&bp, 0, sizeof bp); bp.rho0 = 1.0; bp.T0 = 1.0; }
+  else { std::memset(&bp, 0, sizeof bp); bp.rho0 = 1.0; bp.T0 = 1.0; bp.pml_width_y = -1; }
+  if (bp.periodic_y != 0 && bp.periodic_y != 1) return fail("periodic_y must be 0 or 1");
+  const int Wy = bp.periodic_y ? 0 : (bp.pml_width_y < 0 ? pml_width : bp.pml_width_y);
+  if (bp.periodic_y && bp.pml_width_y > 0) return fail("a periodic y axis has no PML");
+  if (bp.periodic_y && bc == LBM_BC_PERIODIC) return fail("periodic_y needs a ZG or NRBC x edge");
+  if (bp.periodic_y && bc == LBM_BC_NRBC && (bp.edge[0] != 0 || bp.edge[1] != 0))
+    return fail("with periodic_y the W and E edges must be PNR_LODI");
+  if (Wy == 1) return fail("pml_width_y must be 0 or >= 2");
+  if (grid->ny < 8 || grid->nx < 8) return fail("bulk must be at least 8 x 8");
   if (!(bp.rho0 > 0) || !(bp.T0 > 0) || !std::isfinite(bp.u0x) || !std::isfinite(bp.u0y) ||
       !std::isfinite(bp.beta))
     return fail("bad mean state or beta");
@@ -348,7 +359,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   if (!lattice_of(q, ctx->w, &ctx->r, lerr)) { delete ctx; return fail("quadrature failed"); }
   cudaGetDevice(&ctx->device);
 
-  ctx->g = make_geom(grid->nx, grid->ny, pml_width, halo_of(q));
+  ctx->g = make_geom(grid->nx, grid->ny, pml_width, halo_of(q), Wy, bp.periodic_y);
   Geom& g = ctx->g;
 
   switch (q * 2 + (precision == LBM_FP32_DEV)) {
@@ -374,7 +385,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   for (int k = 0; k < 2; ++k) {
     if (cudaMalloc(&ctx->f[k], ctx->fbytes) != cudaSuccess) return oom("populations");
     if (cudaMemset(ctx->f[k], 0, ctx->fbytes) != cudaSuccess) return oom("populations");
-    if (g.W > 0) {
+    if (g.W > 0 || g.Wy > 0) {
       if (cudaMalloc(&ctx->S[k], ctx->sbytes) != cudaSuccess) return oom("PML accumulator");
       if (cudaMemset(ctx->S[k], 0, ctx->sbytes) != cudaSuccess) return oom("PML accumulator");
     }
@@ -722,7 +733,8 @@ lbm_status lbm_checkpoint(lbm_ctx* ctx, void* host, size_t bytes) {
   if (!host || bytes < need) { ctx->err = "checkpoint buffer too small"; return LBM_EINVAL; }
   char* p = static_cast<char*>(host);
   CkptHeader h{kMagic, ctx->q, ctx->g.nx, ctx->g.ny, ctx->g.W, (int64_t)ctx->prec, ctx->steps,
-               (int64_t)(ctx->prev_valid ? 1 : 0) | (int64_t)(ctx->prev_prestream ? 2 : 0)};
+               (int64_t)(ctx->prev_valid ? 1 : 0) | (int64_t)(ctx->prev_prestream ? 2 : 0) |
+                   ((int64_t)ctx->g.py << 2) | ((int64_t)ctx->g.Wy << 8)};
   std::memcpy(p, &h, sizeof h);
   p += sizeof h;
   const cudaMemcpyKind k = cudaMemcpyDeviceToHost;
@@ -745,7 +757,8 @@ lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes) {
   CkptHeader h;
   std::memcpy(&h, p, sizeof h);
   if (h.magic != kMagic || h.q != ctx->q || h.nx != ctx->g.nx || h.ny != ctx->g.ny ||
-      h.W != ctx->g.W || h.prec != (int64_t)ctx->prec) {
+      h.W != ctx->g.W || h.prec != (int64_t)ctx->prec || ((h.flags >> 2) & 1) != ctx->g.py ||
+      (h.flags >> 8) != ctx->g.Wy) {
     ctx->err = "checkpoint does not match this context";
     return LBM_EINVAL;
   }

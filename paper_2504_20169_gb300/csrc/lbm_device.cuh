@@ -17,6 +17,8 @@
 //   k_frame2          PML nodes: the gradient part of Omega^PML (needs the frame's new Q)
 //   k_gamma           the M boundary layers outside F (zero gradient, characteristic BC with
 //                     non-equilibrium extrapolation, or periodic images)
+//   k_wrap_y          periodic y axis only, after all of the above: the M rows beyond each y
+//                     end copy the finished rows they image
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -29,10 +31,13 @@ constexpr int kMaxQ = 37;
 
 struct Geom {
   int nx, ny, W, M, Lx, Ly;
+  int Wy;            // PML layers on the S and N edges (W: on the W and E edges)
+  int py;            // 1: the y axis is periodic (then Wy = 0)
   int pitch;         // storage row length (elements), multiple of 32
   int cF0;           // storage column of x = 0 of F, multiple of 32
   long long plane;   // elements per direction plane (pitch * (Ly + 2M))
-  int Wf;            // frame depth: max(W + 1, M) when W > 0 or periodic, else M
+  int Wf;            // frame depth along x: max(W + 1, M) when W > 0, else M
+  int Wfy;           // frame depth along y: likewise with Wy; 0 on a periodic y axis
   int frame_n;       // number of frame nodes
   long long Sp;      // PML accumulator stride per direction
   int nb;            // characteristic-BC band nodes: 2 M (Lx + Ly)
@@ -64,37 +69,60 @@ __device__ inline int dist_out(const Geom& g, int x, int y) {
   return min(min(x, g.Lx - 1 - x), min(y, g.Ly - 1 - y));
 }
 
-// Frame of depth Wf: bottom rows, top rows, then left and right columns of the middle rows.
+// PML classification of node (x, y) of F: layer index per axis i_x = W - (distance to the
+// nearer x edge) (0 outside the x PML), likewise i_y with Wy; P = {i_x > 0 or i_y > 0}; the
+// accumulator Q is kept on P and on the ring one node inside it along each PML axis. Layer
+// fraction max(i_x / W, i_y / Wy) (Chebyshev in corners; Eq. PML_ramp's i / W for equal widths).
+template <class Real>
+struct PmlNode {
+  bool has_q, in_p;
+  Real frac;
+};
+
+template <class Real>
+__device__ inline PmlNode<Real> pml_node(const Geom& g, int x, int y) {
+  const int dx = min(x, g.Lx - 1 - x), dy = min(y, g.Ly - 1 - y);
+  const int ix = g.W > 0 ? max(0, g.W - dx) : 0;
+  const int iy = g.Wy > 0 ? max(0, g.Wy - dy) : 0;
+  PmlNode<Real> n;
+  n.in_p = ix > 0 || iy > 0;
+  n.has_q = (g.W > 0 && dx <= g.W) || (g.Wy > 0 && dy <= g.Wy);
+  const Real fx = g.W > 0 ? Real(ix) / Real(g.W) : Real(0);
+  const Real fy = g.Wy > 0 ? Real(iy) / Real(g.Wy) : Real(0);
+  n.frac = fx > fy ? fx : fy;
+  return n;
+}
+
+// Frame: bottom rows (Wfy), top rows (Wfy), then left and right columns (Wf) of the middle rows.
 __device__ inline void frame_xy(const Geom& g, int fi, int& x, int& y) {
-  const int Lx = g.Lx, Wf = g.Wf;
-  const int bot = Wf * Lx;
+  const int Lx = g.Lx, Wf = g.Wf, Wfy = g.Wfy;
+  const int bot = Wfy * Lx;
   if (fi < bot) { y = fi / Lx; x = fi - y * Lx; return; }
   fi -= bot;
-  if (fi < bot) { int t = fi / Lx; y = g.Ly - Wf + t; x = fi - t * Lx; return; }
+  if (fi < bot) { int t = fi / Lx; y = g.Ly - Wfy + t; x = fi - t * Lx; return; }
   fi -= bot;
-  const int side = (g.Ly - 2 * Wf) * Wf;
-  if (fi < side) { int t = fi / Wf; y = Wf + t; x = fi - t * Wf; return; }
+  const int side = (g.Ly - 2 * Wfy) * Wf;
+  if (fi < side) { int t = fi / Wf; y = Wfy + t; x = fi - t * Wf; return; }
   fi -= side;
   int t = fi / Wf;
-  y = Wf + t;
+  y = Wfy + t;
   x = g.Lx - Wf + (fi - t * Wf);
 }
 
 __device__ inline int frame_index(const Geom& g, int x, int y) {
-  const int Lx = g.Lx, Wf = g.Wf;
-  if (y < Wf) return y * Lx + x;
-  if (y >= g.Ly - Wf) return Wf * Lx + (y - (g.Ly - Wf)) * Lx + x;
-  const int base = 2 * Wf * Lx;
-  if (x < Wf) return base + (y - Wf) * Wf + x;
-  return base + (g.Ly - 2 * Wf) * Wf + (y - Wf) * Wf + (x - (g.Lx - Wf));
+  const int Lx = g.Lx, Wf = g.Wf, Wfy = g.Wfy;
+  if (y < Wfy) return y * Lx + x;
+  if (y >= g.Ly - Wfy) return Wfy * Lx + (y - (g.Ly - Wfy)) * Lx + x;
+  const int base = 2 * Wfy * Lx;
+  if (x < Wf) return base + (y - Wfy) * Wf + x;
+  return base + (g.Ly - 2 * Wfy) * Wf + (y - Wfy) * Wf + (x - (g.Lx - Wf));
 }
 
-// sigma of Eq. (PML_ramp) at distance d (0 = outermost layer) from the edge of F.
+// sigma of Eq. (PML_ramp) for layer fraction frac = i / W.
 template <class Real>
-__device__ inline Real sigma_at(const Consts<Real>& c, int W, int d) {
-  const Real s = Real(W - d) / Real(W);
+__device__ inline Real sigma_of(const Consts<Real>& c, Real frac) {
   Real p = Real(1);
-  for (int k = 0; k < c.power; ++k) p *= s;
+  for (int k = 0; k < c.power; ++k) p *= frac;
   return c.sigma_max * p;
 }
 
@@ -285,8 +313,8 @@ __global__ void __launch_bounds__(256) k_bulk(Geom g, Consts<Real> c, const Real
                                               Real* __restrict__ B, int* flag) {
   const int x0 = (g.Wf / 32) * 32;
   const int x = x0 + blockIdx.x * 32 + threadIdx.x;
-  const int y = g.Wf + blockIdx.y * blockDim.y + threadIdx.y;
-  if (x < g.Wf || x >= g.Lx - g.Wf || y >= g.Ly - g.Wf) return;
+  const int y = g.Wfy + blockIdx.y * blockDim.y + threadIdx.y;
+  if (x < g.Wf || x >= g.Lx - g.Wf || y >= g.Ly - g.Wfy) return;
   const long long idx = gindex(g, x, y);
   Real p[S::Q];
   load_pop<S, Real, STREAM>(p, A, g, idx);
@@ -338,9 +366,10 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
   const Macro<Real> m = moments<S, Real, DEV>(p, c);
   if (unphysical(m)) *flag = 1;
   if (save_edges && d < 2) save_edge_moments(g, Uedge, x, y, m, c.r);
-  const bool has_q = g.W > 0 && d <= g.W;
-  const bool in_p = g.W > 0 && d < g.W;
-  const Real sig = in_p ? sigma_at(c, g.W, d) : Real(0);
+  const PmlNode<Real> pn = pml_node<Real>(g, x, y);
+  const bool has_q = pn.has_q;
+  const bool in_p = pn.in_p;
+  const Real sig = in_p ? sigma_of(c, pn.frac) : Real(0);
   const EqCoef<Real> k = eq_coef<S::ORDER, Real>(m);
   if (has_q) {
     // all accumulator loads in flight before any store
@@ -374,9 +403,9 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
   if (fi >= g.frame_n) return;
   int x, y;
   frame_xy(g, fi, x, y);
-  const int d = dist_out(g, x, y);
-  if (d >= g.W) return;
-  const Real sig = sigma_at(c, g.W, d);
+  const PmlNode<Real> pn = pml_node<Real>(g, x, y);
+  if (!pn.in_p) return;
+  const Real sig = sigma_of(c, pn.frac);
   // x axis: neighbours / one-sided stencil
   int ax0, ax1, ax2;  // frame indices; derivative = cx0*Q(ax0) + cx1*Q(ax1) + cx2*Q(ax2)
   Real cx0, cx1, cx2;
@@ -392,7 +421,12 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
   }
   int ay0, ay1, ay2;
   Real cy0, cy1, cy2;
-  if (y == 0) {
+  if (g.py) {  // periodic y: central difference with wrap
+    ay0 = frame_index(g, x, y + 1 < g.Ly ? y + 1 : 0);
+    ay1 = frame_index(g, x, y > 0 ? y - 1 : g.Ly - 1);
+    ay2 = fi;
+    cy0 = Real(0.5); cy1 = Real(-0.5); cy2 = Real(0);
+  } else if (y == 0) {
     ay0 = fi; ay1 = frame_index(g, x, 1); ay2 = frame_index(g, x, 2);
     cy0 = Real(-1.5); cy1 = Real(2); cy2 = Real(-0.5);
   } else if (y == g.Ly - 1) {
@@ -450,6 +484,9 @@ __global__ void __launch_bounds__(128) k_gamma(Geom g, Consts<Real> c, BcParams 
   if (t >= g.ngamma) return;
   int x, y;
   gamma_xy(g, t, x, y);
+  // rows beyond a periodic y axis are copied from the finished rows they image (k_wrap_y)
+  if (g.py && (y < 0 || y >= g.Ly)) return;
+  const long long dst = gindex(g, x, y);
   int sx, sy;
   if (bc.bc == 0) {
     sx = (x + g.Lx) % g.Lx;
@@ -461,7 +498,6 @@ __global__ void __launch_bounds__(128) k_gamma(Geom g, Consts<Real> c, BcParams 
   Real p[S::Q];
   load_pop<S, Real, STREAM>(p, A, g, gindex(g, sx, sy));
   const Macro<Real> m = moments<S, Real, DEV>(p, c);
-  const long long dst = gindex(g, x, y);
   const bool xo = x < 0 || x >= g.Lx, yo = y < 0 || y >= g.Ly;
   if (bc.bc == 2 && xo != yo) {
     // edge band node: index into the target arrays
@@ -494,6 +530,21 @@ __global__ void __launch_bounds__(128) k_gamma(Geom g, Consts<Real> c, BcParams 
   collide_bgk<S, Real, DEV>(p, m, c);
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) B[(long long)i * g.plane + dst] = p[i];
+}
+
+// Periodic y axis: the M rows below y = 0 and above y = Ly - 1 (boundary columns included)
+// take the post-collision populations of the rows they image, PML term included, once every
+// other kernel of the step has written B. Thread = (direction, row pair j, column).
+template <class Real>
+__global__ void __launch_bounds__(256) k_wrap_y(Geom g, Real* __restrict__ B) {
+  const int Gx = g.Lx + 2 * g.M;
+  const long long n = (long long)Gx * g.M;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int j = int(t / Gx) + 1, x = int(t % Gx) - g.M;
+  Real* plane = B + (long long)blockIdx.y * g.plane;
+  plane[gindex(g, x, -j)] = plane[gindex(g, x, g.Ly - j)];
+  plane[gindex(g, x, g.Ly - 1 + j)] = plane[gindex(g, x, j - 1)];
 }
 
 // ------------------------------------------------------------------------------------------

@@ -75,6 +75,7 @@ __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
   else if (k < 2 * cw) { e = 1; k -= cw; }
   else if (k < 2 * cw + cs) { e = 2; k -= 2 * cw; }
   else { e = 3; k -= 2 * cw + cs; }
+  if (g.py && e >= 2) return;   // no S / N boundary on a periodic y axis
   const int len = e < 2 ? Ly : Lx;
   const int off = e == 0 ? 0 : e == 1 ? M * Ly : e == 2 ? 2 * M * Ly : 2 * M * Ly + M * Lx;
   const int ueoff = e == 0 ? 0 : e == 1 ? 2 * Ly : e == 2 ? 4 * Ly : 4 * Ly + 2 * Lx;

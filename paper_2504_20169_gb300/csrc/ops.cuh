@@ -31,8 +31,7 @@ __global__ void k_init_eq(Geom g, Consts<Real> c, const double* __restrict__ rho
   m.theta = Real(T0 - 1.0);
   const EqCoef<Real> kc = eq_coef<S::ORDER, Real>(m);
   const long long idx = gindex(g, x, y);
-  const int d = dist_out(g, x, y);
-  const bool has_q = g.W > 0 && d <= g.W;
+  const bool has_q = pml_node<Real>(g, x, y).has_q;
   const int fi = has_q ? frame_index(g, x, y) : 0;
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) {
@@ -88,7 +87,7 @@ __global__ void __launch_bounds__(256) k_fields(Geom g, Consts<Real> c, const Re
                                                 const double* r2, const double* r3,
                                                 double* partials, int mode) {
   const int nxr = region ? g.Lx : g.nx, nyr = region ? g.Ly : g.ny;
-  const int off = region ? 0 : g.W;
+  const int offx = region ? 0 : g.W, offy = region ? 0 : g.Wy;
   const int xr = blockIdx.x * blockDim.x + threadIdx.x;
   const int yr = blockIdx.y * blockDim.y + threadIdx.y;
   const bool live = xr < nxr && yr < nyr;
@@ -103,7 +102,7 @@ __global__ void __launch_bounds__(256) k_fields(Geom g, Consts<Real> c, const Re
   }
   if (live) {
     Real p[S::Q];
-    load_pop<S, Real, STREAM>(p, A, g, gindex(g, xr + off, yr + off));
+    load_pop<S, Real, STREAM>(p, A, g, gindex(g, xr + offx, yr + offy));
     const Macro<Real> m = moments<S, Real, DEV>(p, c);
     const double rho = double(m.rho), ux = double(m.urx / c.r), uy = double(m.ury / c.r);
     const double T = 1.0 + double(m.theta);
@@ -194,7 +193,7 @@ struct Ops {
     mark(4, bs);
     bool fused = false;
     if constexpr (DEV) {
-      if (g.W > 0) {
+      if (g.W > 0 || g.Wy > 0) {
         // FP32: single-pass frame (tile + halo in shared memory)
         const FrameTiles ft = make_frame_tiles(g, 256);
         const size_t smem = pml_fused_smem<S>(ft);
@@ -210,7 +209,7 @@ struct Ops {
           d.bc.bc == 2 ? 1 : 0, d.flag);
     mark(5, bs);
     mark(6, bs);
-    if (g.W > 0 && !fused)
+    if ((g.W > 0 || g.Wy > 0) && !fused)
       k_frame2<S, Real><<<(g.frame_n + 127) / 128, 128, 0, bs>>>(
           g, c, B, static_cast<const Real*>(d.Sold), static_cast<const Real*>(d.Snew));
     mark(7, bs);
@@ -219,7 +218,7 @@ struct Ops {
                                                                           d.Vtgt);
     mark(9, bs);
     const int nbx = (g.Lx - g.Wf - (g.Wf / 32) * 32 + 31) / 32;
-    const int ny_in = g.Ly - 2 * g.Wf;
+    const int ny_in = g.Ly - 2 * g.Wfy;
     constexpr int BY = 4;
     mark(2, d.st);
     if (nbx > 0 && ny_in > 0) {
@@ -230,6 +229,10 @@ struct Ops {
     if (d.aux) {
       cudaEventRecord(d.join, d.aux);
       cudaStreamWaitEvent(d.st, d.join, 0);
+    }
+    if (g.py) {
+      const long long n = (long long)(g.Lx + 2 * g.M) * g.M;
+      k_wrap_y<Real><<<dim3(unsigned((n + 255) / 256), S::Q), 256, 0, d.st>>>(g, B);
     }
     return cudaGetLastError();
   }

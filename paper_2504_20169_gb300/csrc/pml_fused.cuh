@@ -1,9 +1,10 @@
 // Single-pass PML frame kernel (FP32 deviation storage): one block per tile of the frame
 // (P + inner ring, distance < Wf from the edge of F) with a 2-node halo.
 //
-//  A  every node of tile + halo that carries Q (distance <= W) pulls its populations, takes
-//     its moments and stores Q_i = S_i^(n-1) + f_hat_i^n / 2 for all i in shared memory
-//     (trapezoidal accumulator, Eq. PMLQ; f_hat = f_eq - f_eq_bar, Eq. decomp-NJ);
+//  A  every owned node and every node of tile + halo that carries Q (distance <= W along a
+//     PML axis) pulls its populations and takes its moments; the latter store
+//     Q_i = S_i^(n-1) + f_hat_i^n / 2 for all i in shared memory (trapezoidal accumulator,
+//     Eq. PMLQ; f_hat = f_eq - f_eq_bar, Eq. decomp-NJ);
 //  C  every owned node pulls again (cache hits), collides with BGK (moments kept from A),
 //     adds on P the PML term of Eq. (PMLCOLL) with grad Q from shared memory
 //     (Eq. FD-dx-center; Eq. FD-dx-bw along the outward normal on the outermost layer; the
@@ -26,15 +27,15 @@ struct FrameTiles {
 
 inline FrameTiles make_frame_tiles(const Geom& g, int threads) {
   FrameTiles t{};
-  const int Wf = g.Wf;
-  t.tb_rows = (Wf + 7) / 8;
-  t.tb_h = (Wf + t.tb_rows - 1) / t.tb_rows;
+  const int Wf = g.Wf, Wfy = g.Wfy;
+  t.tb_rows = (Wfy + 7) / 8;
+  t.tb_h = t.tb_rows > 0 ? (Wfy + t.tb_rows - 1) / t.tb_rows : 1;
   t.tb_cols = (g.Lx + 31) / 32;
   t.s_cols = (Wf + 31) / 32;
   t.s_w = (Wf + t.s_cols - 1) / t.s_cols;
   t.s_h = threads / t.s_w;
   if (t.s_h > 32) t.s_h = 32;
-  t.s_rows = (g.Ly - 2 * Wf + t.s_h - 1) / t.s_h;
+  t.s_rows = (g.Ly - 2 * Wfy + t.s_h - 1) / t.s_h;
   t.n_tb = 2 * t.tb_rows * t.tb_cols;
   t.n_side = 2 * t.s_cols * t.s_rows;
   const int e1 = (32 + 4) * (t.tb_h + 4), e2 = (t.s_w + 4) * (t.s_h + 4);
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
       tw = 32;
       th = ft.tb_h;
       x0 = cc * 32;
-      y0 = band == 0 ? r * th : g.Ly - g.Wf + r * th;
+      y0 = band == 0 ? r * th : g.Ly - g.Wfy + r * th;
     } else {
       k -= ft.n_tb;
       const int per = ft.s_cols * ft.s_rows;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
       tw = ft.s_w;
       th = ft.s_h;
       x0 = band == 2 ? cc * tw : g.Lx - g.Wf + cc * tw;
-      y0 = g.Wf + r * th;
+      y0 = g.Wfy + r * th;
     }
   }
   const int ew = tw + 4, eh = th + 4, next = ew * eh;
@@ -90,15 +91,19 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   // ---- A: Q on tile + halo; equilibria and moments of the owned nodes kept for phase C
   for (int e = tid; e < next; e += blockDim.x) {
     const int ex = e % ew, ey = e / ew;
-    const int x = x0 - 2 + ex, y = y0 - 2 + ey;
-    if (x < 0 || y < 0 || x >= g.Lx || y >= g.Ly || dist_out(g, x, y) > g.W) continue;
+    const int x = x0 - 2 + ex;
+    int y = y0 - 2 + ey;
+    if (g.py) y = (y + g.Ly) % g.Ly;   // halo rows wrap along a periodic y axis
+    if (x < 0 || y < 0 || x >= g.Lx || y >= g.Ly) continue;
+    const int tx = ex - 2, ty = ey - 2;
+    const int own = (tx >= 0 && ty >= 0 && tx < tw && ty < th) ? ty * tw + tx : -1;
+    // frame nodes farther out than the PML along neither axis (a frame depth set by M
+    // where an axis has no PML) still need their moments for phase C
+    const bool hq = pml_node<float>(g, x, y).has_q;
+    if (!hq && own < 0) continue;
     float p[S::Q];
     load_pop<S, float, STREAM>(p, A, g, gindex(g, x, y));
     const Macro<float> m = moments<S, float, true>(p, c);
-    const EqCoef<float> kc = eq_coef<S::ORDER, float>(m);
-    const int fi = frame_index(g, x, y);
-    const int tx = ex - 2, ty = ey - 2;
-    const int own = (tx >= 0 && ty >= 0 && tx < tw && ty < th) ? ty * tw + tx : -1;
     if (own >= 0) {
       Mc[0 * 256 + own] = m.rho;
       Mc[1 * 256 + own] = m.drho;
@@ -108,6 +113,9 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
       Mc[5 * 256 + own] = m.u2;
       Mc[6 * 256 + own] = m.theta;
     }
+    if (!hq) continue;
+    const EqCoef<float> kc = eq_coef<S::ORDER, float>(m);
+    const int fi = frame_index(g, x, y);
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       const float eq = eq_dir<S, float, true>(i, m, kc, c);
@@ -122,10 +130,10 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   const int x = x0 + tx, y = y0 + ty;
   if (x >= g.Lx || y >= g.Ly) return;
   bool owned;
-  if (band == 0) owned = y < g.Wf;
-  else if (band == 1) owned = y >= g.Ly - g.Wf;
-  else if (band == 2) owned = x < g.Wf && y < g.Ly - g.Wf;
-  else owned = y < g.Ly - g.Wf;
+  if (band == 0) owned = y < g.Wfy;
+  else if (band == 1) owned = y >= g.Ly - g.Wfy;
+  else if (band == 2) owned = x < g.Wf && y < g.Ly - g.Wfy;
+  else owned = y < g.Ly - g.Wfy;
   if (!owned) return;
   const int d = dist_out(g, x, y);
   const long long idx = gindex(g, x, y);
@@ -144,15 +152,18 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   const EqCoef<float> kc = eq_coef<S::ORDER, float>(m);
   const int fi = frame_index(g, x, y);
   const int e0 = (ty + 2) * ew + (tx + 2);
-  const bool in_p = d < g.W;
-  const float sig = in_p ? sigma_at(c, g.W, d) : 0.f;
+  const PmlNode<float> pn = pml_node<float>(g, x, y);
+  const bool in_p = pn.in_p;
+  const float sig = in_p ? sigma_of(c, pn.frac) : 0.f;
   // gradient stencils on the shared-memory tile (offsets in extended-tile units)
   float cx0 = 0.5f, cx1 = -0.5f, cx2 = 0.f, cy0 = 0.5f, cy1 = -0.5f, cy2 = 0.f;
   int ox0 = 1, ox1 = -1, ox2 = 0, oy0 = ew, oy1 = -ew, oy2 = 0;
   if (x == 0) { cx0 = -1.5f; cx1 = 2.f; cx2 = -0.5f; ox0 = 0; ox1 = 1; ox2 = 2; }
   else if (x == g.Lx - 1) { cx0 = 1.5f; cx1 = -2.f; cx2 = 0.5f; ox0 = 0; ox1 = -1; ox2 = -2; }
-  if (y == 0) { cy0 = -1.5f; cy1 = 2.f; cy2 = -0.5f; oy0 = 0; oy1 = ew; oy2 = 2 * ew; }
-  else if (y == g.Ly - 1) { cy0 = 1.5f; cy1 = -2.f; cy2 = 0.5f; oy0 = 0; oy1 = -ew; oy2 = -2 * ew; }
+  if (!g.py && y == 0) { cy0 = -1.5f; cy1 = 2.f; cy2 = -0.5f; oy0 = 0; oy1 = ew; oy2 = 2 * ew; }
+  else if (!g.py && y == g.Ly - 1) {
+    cy0 = 1.5f; cy1 = -2.f; cy2 = 0.5f; oy0 = 0; oy1 = -ew; oy2 = -2 * ew;
+  }
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) {
     const float eq = eq_dir<S, float, true>(i, m, kc, c);

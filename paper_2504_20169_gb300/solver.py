@@ -40,12 +40,15 @@ def _host(a):
 class Solver:
     def __init__(self, nx, ny, W, tau, sigma_max=0.0, sigma_power=2, bc="zg", q=37,
                  nrbc_edges=(0, 0, 0, 0), beta=0.0, mean=(1.0, 0.0, 0.0, 1.0), relax_sign=-1.0,
-                 precision="fp64", stream=None):
+                 precision="fp64", stream=None, pml_width_y=None, periodic_y=False):
+        """W: PML layers on the W/E edges (and S/N unless pml_width_y is given); periodic_y:
+        the y axis wraps (no S/N boundary, no PML there)."""
         import torch
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.nx, self.ny, self.W, self.q = nx, ny, W, q
-        self.Lx, self.Ly = nx + 2 * W, ny + 2 * W
+        self.Wy = 0 if periodic_y else (W if pml_width_y is None else pml_width_y)
+        self.Lx, self.Ly = nx + 2 * W, ny + 2 * self.Wy
         self.precision = precision
         grid = L.lbm_grid(nx, ny)
         sig = L.lbm_sigma_profile(sigma_max, sigma_power)
@@ -55,6 +58,8 @@ class Solver:
         bp.beta = beta
         bp.relax_sign = relax_sign
         bp.rho0, bp.u0x, bp.u0y, bp.T0 = mean
+        bp.pml_width_y = -1 if pml_width_y is None else int(pml_width_y)
+        bp.periodic_y = 1 if periodic_y else 0
         out = C.c_void_p()
         with torch.cuda.device(self.stream.device):
             _check(L.lib().lbm_create(C.byref(grid), q, float(tau), W, C.byref(sig), _BC[bc],

@@ -7,7 +7,8 @@ from oracle import OracleLBM
 
 def case_kwargs(**kw):
     base = dict(nx=32, ny=32, W=4, tau=0.8, sigma_max=0.1, sigma_power=3, bc="zg", q=37,
-                nrbc_edges=(0, 0, 0, 0), beta=0.0, mean=(1.0, 0.0, 0.0, 1.0), relax_sign=-1.0)
+                nrbc_edges=(0, 0, 0, 0), beta=0.0, mean=(1.0, 0.0, 0.0, 1.0), relax_sign=-1.0,
+                Wy=None, periodic_y=False)
     base.update(kw)
     return base
 
@@ -15,7 +16,8 @@ def case_kwargs(**kw):
 def run_oracle(kw, fields, steps):
     o = OracleLBM(kw["nx"], kw["ny"], kw["W"], kw["tau"], kw["sigma_max"], kw["sigma_power"],
                   kw["bc"], q=kw["q"], nrbc_edges=kw["nrbc_edges"], beta=kw["beta"],
-                  mean=kw["mean"], relax_sign=kw["relax_sign"])
+                  mean=kw["mean"], relax_sign=kw["relax_sign"], Wy=kw["Wy"],
+                  periodic_y=kw["periodic_y"])
     o.init(*fields)
     o.step(steps)
     return o.fields(), o
@@ -25,7 +27,8 @@ def make_solver(kw, precision="fp64"):
     from paper_2504_20169_gb300 import Solver
     return Solver(kw["nx"], kw["ny"], kw["W"], kw["tau"], kw["sigma_max"], kw["sigma_power"],
                   kw["bc"], kw["q"], kw["nrbc_edges"], kw["beta"], kw["mean"],
-                  kw["relax_sign"], precision)
+                  kw["relax_sign"], precision, pml_width_y=kw["Wy"],
+                  periodic_y=kw["periodic_y"])
 
 
 def run_gpu(kw, fields, steps, precision="fp64"):

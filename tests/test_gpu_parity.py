@@ -122,6 +122,36 @@ def test_parity_nrbc_band_lengths(nx, ny, W, steps, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+@pytest.mark.parametrize("bc,W", [("zg", 0), ("zg", 8), ("nrbc", 0), ("nrbc", 8)])
+def test_parity_periodic_y_axis(bc, W, precision):
+    """Sec. 5.1 setting: periodic y axis, PML (or none) and ZG / PNR-LODI on the x edges. The
+    density step of Sec. 5.1 plus a y-dependent smooth perturbation, so that the wrapped rows,
+    the wrapped halo of the frame kernel and the y-central PML gradient all matter."""
+    nx, ny = 60, 20
+    kw = case_kwargs(nx=nx, ny=ny, W=W, tau=0.7, sigma_max=0.05, sigma_power=2, bc=bc,
+                     mean=(1.0, 0.05, 0.0, 1.0), Wy=0, periodic_y=True)
+    rho, ux, uy, T = wl.density_step(nx, ny, Ma=0.05, W=W, Wy=0)
+    pr, pux, puy, pT = wl.random_smooth_state(nx, ny, W, seed=21, du=0.02, Wy=0)
+    fields = (rho + pr - 1.0, ux + pux, uy + puy, T + pT - 1.0)
+    check(kw, fields, 40, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+@pytest.mark.parametrize("nx,ny,W,Wy,bc", [(40, 30, 6, 3, "zg"), (36, 44, 0, 5, "nrbc"),
+                                           (50, 26, 7, 0, "zg"), (30, 34, 2, 9, "nrbc")])
+def test_parity_per_axis_pml_widths(nx, ny, W, Wy, bc, precision):
+    """Different PML widths on the x and y edges (one of them possibly 0): frame depths per
+    axis, the layer fraction max(i_x / W, i_y / Wy) in the corners, Q support per axis.
+    PNR-LODI edges: with CBC relax next to unequal widths the oracle itself diverges within
+    40 steps on these grids."""
+    kw = case_kwargs(nx=nx, ny=ny, W=W, tau=0.75, sigma_max=0.15, sigma_power=2, bc=bc,
+                     nrbc_edges=(0, 0, 0, 0), mean=(1.0, 0.05, 0.02, 1.0), Wy=Wy)
+    fields = wl.random_smooth_state(nx, ny, W, seed=nx * ny + W, du=0.04,
+                                    mean_u=(0.05, 0.02), Wy=Wy)
+    check(kw, fields, 30, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
 @pytest.mark.parametrize("q", [17, 9])
 @pytest.mark.parametrize("bc", ["zg", "nrbc"])
 def test_parity_other_stencils(q, bc, precision):

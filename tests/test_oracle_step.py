@@ -210,3 +210,60 @@ def test_acoustic_pulse_against_linear_closed_form():
         0, 12 * math.sqrt(a), limit=400)[0] for r in rr])
     got = p[row, xs]
     assert np.max(np.abs(got - want)) < 0.005 * amp   # measured 0.11 %; isothermal c: 18 %
+
+
+@pytest.mark.parametrize("bc,W", [("zg", 0), ("zg", 6), ("nrbc", 6)])
+def test_periodic_y_keeps_a_y_invariant_state_y_invariant(bc, W):
+    """Sec. 5.1 setting: a density step that does not depend on y, on a y-periodic grid with
+    PML / outflow BC on the x edges, stays y-invariant, and the row does not depend on ny (a
+    wrong wrap or a y-boundary treatment applied on the periodic axis breaks both)."""
+    rows = []
+    for ny in (8, 11):
+        o = OracleLBM(40, ny, W, 0.7, 0.05, 2, bc, periodic_y=True)
+        o.init(*wl.density_step(40, ny, Ma=0.05, W=W, Wy=0))
+        o.step(25)
+        rho = o.fields("F")[0]
+        assert rho.shape == (ny, 40 + 2 * W)
+        assert np.array_equal(rho, np.broadcast_to(rho[0], rho.shape))
+        rows.append(rho[0])
+    assert np.array_equal(rows[0], rows[1])
+    assert np.abs(rows[0][W:W + 40] - rows[0][W:W + 40].mean()).max() > 1e-3
+
+
+def test_periodic_y_light_cone_matches_fully_periodic_run():
+    """Away from the x edges a y-periodic run equals a fully periodic one bit for bit."""
+    nx, ny, n = 40, 14, 3
+    fields = wl.random_smooth_state(nx, ny, 0, seed=5)
+    a = OracleLBM(nx, ny, 0, 0.7, bc="zg", periodic_y=True)
+    b = OracleLBM(nx, ny, 0, 0.7, bc="periodic")
+    a.init(*fields)
+    b.init(*fields)
+    a.step(n)
+    b.step(n)
+    d = 4 * n + 1
+    fa, fb = a.fields(), b.fields()
+    for za, zb in zip(fa, fb):
+        assert np.array_equal(za[:, d:nx - d], zb[:, d:nx - d])
+    assert not np.array_equal(fa[0], fb[0])
+
+
+def test_per_axis_pml_widths_transpose():
+    """W on the x edges and Wy on the y edges: the run of the transposed problem, with the
+    widths swapped, is the transposed run (catches a width used on the wrong axis)."""
+    nx, ny, W, Wy = 30, 22, 6, 3
+    a = OracleLBM(nx, ny, W, 0.7, 0.1, 2, "zg", Wy=Wy)
+    b = OracleLBM(ny, nx, Wy, 0.7, 0.1, 2, "zg", Wy=W)
+    c = (11.0, 7.0)
+    a.init(*wl.pressure_pulse(nx, ny, W, amp=1e-3, halfwidth=3.0, center=c, Wy=Wy))
+    b.init(*wl.pressure_pulse(ny, nx, Wy, amp=1e-3, halfwidth=3.0, center=c[::-1], Wy=W))
+    a.step(40)
+    b.step(40)
+    ra, rb = a.fields("F")[0] - 1.0, b.fields("F")[0] - 1.0
+    assert ra.shape == (ny + 2 * Wy, nx + 2 * W)
+    assert np.abs(ra[:, :W]).max() > 1e-8          # the pulse has reached both PML slabs
+    assert np.abs(ra[:Wy, :]).max() > 1e-8
+    assert np.max(np.abs(ra - rb.T)) < 1e-13
+    sa = pml.sigma_field(nx + 2 * W, ny + 2 * Wy, W, 0.1, 2, Wy)
+    assert sa[Wy + 5, 0] == pytest.approx(0.1) and sa[0, W + 5] == pytest.approx(0.1)
+    assert sa[Wy + 5, 1] == pytest.approx(0.1 * (5 / 6) ** 2)
+    assert sa[1, W + 5] == pytest.approx(0.1 * (2 / 3) ** 2)

@@ -28,14 +28,16 @@ import numpy as np
 GAMMA = 2.0  # (D + 2) / D for D = 2, monatomic ideal gas
 
 
-def f_shape(nx: int, ny: int, W: int) -> tuple[int, int]:
-    """(Ly, Lx) of the fluid region F."""
-    return (ny + 2 * W, nx + 2 * W)
+def f_shape(nx: int, ny: int, W: int, Wy: int | None = None) -> tuple[int, int]:
+    """(Ly, Lx) of the fluid region F (W PML layers on the x edges, Wy, default W, on y)."""
+    Wy = W if Wy is None else Wy
+    return (ny + 2 * Wy, nx + 2 * W)
 
 
-def _bulk_coords(nx, ny, W):
-    Ly, Lx = f_shape(nx, ny, W)
-    y, x = np.meshgrid(np.arange(Ly, dtype=np.float64) - W,
+def _bulk_coords(nx, ny, W, Wy=None):
+    Wy = W if Wy is None else Wy
+    Ly, Lx = f_shape(nx, ny, W, Wy)
+    y, x = np.meshgrid(np.arange(Ly, dtype=np.float64) - Wy,
                        np.arange(Lx, dtype=np.float64) - W, indexing="ij")
     return x, y
 
@@ -45,9 +47,9 @@ def uniform(nx, ny, W, rho=1.0, ux=0.0, uy=0.0, T=1.0):
     return (np.full(shp, rho), np.full(shp, ux), np.full(shp, uy), np.full(shp, T))
 
 
-def pressure_pulse(nx, ny, W, amp=1e-3, halfwidth=4.0, u0=(0.0, 0.0), center=None):
+def pressure_pulse(nx, ny, W, amp=1e-3, halfwidth=4.0, u0=(0.0, 0.0), center=None, Wy=None):
     """Isentropic Gaussian pressure pulse on a uniform state (rho = T = 1)."""
-    x, y = _bulk_coords(nx, ny, W)
+    x, y = _bulk_coords(nx, ny, W, Wy)
     cx, cy = center if center is not None else ((nx - 1) / 2.0, (ny - 1) / 2.0)
     r2 = (x - cx) ** 2 + (y - cy) ** 2
     p = 1.0 + amp * np.exp(-math.log(2.0) * r2 / (halfwidth * halfwidth))
@@ -84,9 +86,12 @@ def isentropic_vortex(nx, ny, W, R=20.0, Mv=0.05, mean_u=(0.3, 0.0), T0=1.0, rho
     return rho, ux, uy, T
 
 
-def density_step(Lx, Ly, Ma=0.05, rho0=1.0, rho1=1.05, s=0.5, W=0):
-    """Sec. 5.1 density step on an Lx x Ly bulk (periodic in y in the paper), padded by W."""
-    x, _ = _bulk_coords(Lx, Ly, W)
+def density_step(Lx, Ly, Ma=0.05, rho0=1.0, rho1=1.05, s=0.5, W=0, Wy=None):
+    """Sec. 5.1 density step on an Lx x Ly bulk (periodic in y in the paper), padded by W
+    nodes on the x edges and Wy (default W) on the y edges; flat rho0 outside the profile."""
+    Wy = W if Wy is None else Wy
+    y, x = np.meshgrid(np.arange(Ly + 2 * Wy, dtype=np.float64) - Wy,
+                       np.arange(Lx + 2 * W, dtype=np.float64) - W, indexing="ij")
     xs = x + 1.0  # the paper counts nodes from 1
     half = (rho1 - rho0) / 2.0
     left = rho1 + half * (np.tanh(s * (xs - 0.25 * Lx)) - 1.0)
@@ -116,10 +121,10 @@ def paper_vortex(nx, ny, W, Ma=0.1, b=0.2, rstar=0.5, K=180.0, rho0=1.0, T0=1.0,
 
 
 def random_smooth_state(nx, ny, W, seed, du=0.05, drho=0.02, dT=0.02, mean_u=(0.0, 0.0),
-                        modes=4):
+                        modes=4, Wy=None):
     """Seeded smooth random perturbation (sum of low Fourier modes) around a mean state."""
     rng = np.random.default_rng(seed)
-    x, y = _bulk_coords(nx, ny, W)
+    x, y = _bulk_coords(nx, ny, W, Wy)
     Ly, Lx = x.shape
     out = []
     for amp, base in ((drho, 1.0), (du, mean_u[0]), (du, mean_u[1]), (dT, 1.0)):
