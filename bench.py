@@ -109,6 +109,14 @@ class Clocks:
         for line in self.proc.stdout:
             self.rows.append([c.strip() for c in line.split(",")])
 
+    def wait_first(self, timeout=15.0):
+        """Block until the sampler has printed its first row (nvidia-smi start-up can stall
+        the driver for seconds; that must not land inside the timed region)."""
+        t0 = time.time()
+        while self.proc and not self.rows and time.time() - t0 < timeout:
+            time.sleep(0.05)
+        time.sleep(0.3)
+
     def stop(self):
         if not self.proc:
             return None
@@ -205,7 +213,7 @@ def timed_run(Solver, c, fields, precision, steps, warmup, dev, window, prof_ste
     per, total, done = [], 0.0, 0
     torch.cuda.synchronize()
     clocks = Clocks(dev)
-    time.sleep(0.3)
+    clocks.wait_first()
     while done < steps:
         n = min(window, steps - done)
         s.init(*fields)

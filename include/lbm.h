@@ -13,7 +13,8 @@
  *     non-equilibrium extrapolation.
  *
  * Geometry. Bulk nx x ny nodes; W PML layers on every side give the fluid region F of
- * Lx x Ly = (nx + 2W) x (ny + 2W) nodes (Fig. 2); M boundary layers outside F (M = 3 for D2Q37
+ * Lx x Ly = (nx + 2W) x (ny + 2W) nodes (Fig. 2) (with per-edge widths, see lbm_bc_params:
+ * Lx = nx + W_w + W_e, Ly = ny + W_s + W_n); M boundary layers outside F (M = 3 for D2Q37
  * and D2Q17, 1 for D2Q9) hold the boundary nodes x_(b,j) of Sec. 4. Field arrays passed through
  * this ABI are float64, row-major with y outer: element (y, x) at index y * Lx + x over F, or
  * y * nx + x over the bulk.
@@ -69,25 +70,29 @@ typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1 } lbm_precision;
 
 typedef struct { int nx, ny; } lbm_grid;
 
-/* Eq. (PML_ramp): sigma = sigma_max (i / W)^power on PML layer i = 1..W (power 2 in the
- * paper). Corner layers use the larger layer fraction max(i_x / W_x, i_y / W_y). */
-typedef struct { double sigma_max; int power; } lbm_sigma_profile;
+/* Eq. (PML_ramp): sigma = sigma_max (i / W)^power on PML layer i = 1..W of an edge of width W
+ * (power 2 in the paper); a node's layer fraction along an axis is i / W of the nearer edge.
+ * split = 0: sigma_x = sigma_y = sigma(max(f_x, f_y)), Eq. (PMLCOLL) (the paper's choice;
+ * corners by the larger fraction). split = 1: the general form of Eq. (pml-general) with
+ * sigma_x = sigma(f_x), sigma_y = sigma(f_y), each zero outside the slab of its own axis. */
+typedef struct { double sigma_max; int power; int split; } lbm_sigma_profile;
 
 typedef struct {
   int edge[4];                  /* lbm_nrbc_variant for the W, E, S, N edges               */
   double beta;                  /* relaxation Mach number "Ma" of Eq. (CBC-Relax)            */
   double relax_sign;            /* -1 (default reading) or +1 (as printed); 0 means -1      */
   double rho0, u0x, u0y, T0;    /* mean state: f_eq_bar of the PML (Eq. decomp-NJ)          */
-  int pml_width_y;              /* PML layers on the S and N edges; negative: pml_width.    */
-                                /* (A zero-filled struct therefore has no PML on S and N.)  */
+  int use_pml_widths;           /* 0: pml_width on every edge; 1: pml_widths below          */
+  int pml_widths[4];            /* PML layers on the W, E, S, N edges (0 or 2..4096); thin  */
+                                /* layers away from the outlet (closing remark of Sec. 5)   */
   int periodic_y;               /* 1: the y axis is periodic (Sec. 5.1 setting): no S / N    */
-                                /* boundary, requires pml_width_y <= 0 and, with LBM_BC_NRBC, */
-                                /* PNR_LODI on the W and E edges                             */
+                                /* boundary and no PML there (with use_pml_widths = 0 the    */
+                                /* S / N widths are taken as 0; otherwise they must be 0)    */
 } lbm_bc_params;
 
 /* Create a context. tau > 1/2 (tau = +INFINITY gives collisionless free streaming);
- * pml_width 0 or >= 2 (the one-sided gradient reaches two nodes inward); bc_params may be NULL
- * for the rest state (1, 0, 0, 1) and PNR_LODI on every edge. cuda_stream is a cudaStream_t
+ * pml_width 0 or 2..4096 (the one-sided gradient reaches two nodes inward); bc_params may be
+ * NULL for the rest state (1, 0, 0, 1), PNR_LODI on every edge and pml_width on every edge. cuda_stream is a cudaStream_t
  * (NULL = the legacy default stream). Allocates the populations (2 x q x |grid| values of the
  * precision), the PML accumulator on the PML and its inner ring, and the boundary targets. On
  * failure *out is NULL and nothing stays allocated. */
@@ -133,7 +138,9 @@ lbm_status lbm_error_sums(lbm_ctx* ctx, const double* ref_rho, const double* ref
  * e: 2*q ints (ex, ey per velocity), w: q doubles, r: scale. Any output may be NULL. */
 lbm_status lbm_lattice_info(lbm_stencil stencil, int* q, int* e, double* w, double* r);
 
-/* Grid description of a context: out[0..7] = nx, ny, W, M, Lx, Ly, q, step count. */
+/* Grid description of a context: out[0..11] = nx, ny, W (of the W edge), M, Lx, Ly, q, step
+ * count, then the PML widths of the W, E, S, N edges. Lx = nx + W_w + W_e, Ly = ny + W_s + W_n;
+ * the bulk starts at (W_w, W_s) of F. */
 lbm_status lbm_geometry(const lbm_ctx* ctx, int64_t* out);
 
 /* Debug / checkpoint: the stored post-collision populations of the last completed step (or

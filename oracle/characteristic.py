@@ -14,11 +14,12 @@ Eq. (thermal_LODI_macro_evo): dU/dt = -S^-1 L_bar.
 
 Readings where the paper defers to its ref. [klass-camwa-2024] (not available):
 * Boundary nodes are the M = 3 layers outside F. Each edge node carries its own target U_tgt,
-  advanced by one explicit Euler step per time step from the time-n state.
+  advanced over one time step by classical RK4 with the fluid moments frozen at time n
+  (solver.py; explicit Euler is unstable here).
 * Normal derivative at a boundary node x_b: one-sided second order along the outward normal n,
   (3 U(x_b) - 4 U(x_b - n) + U(x_b - 2n)) / 2, using U_tgt for boundary nodes and the moments
   for fluid nodes. Tangential derivative: central along the boundary layer, one-sided second
-  order at the two ends of the layer.
+  order at the two ends of the layer (central with wrap-around along a periodic axis).
 * Lattice spacing: a population with xi_i = r e_i crosses e_i nodes per step, so one node is r
   normalized length units and d/dx = (1/r) d/d(node index).
 * Incoming waves are those with Lambda_k * (outward sign) < 0.
@@ -110,8 +111,11 @@ def one_sided(u0, u1, u2):
     return 0.5 * (3.0 * u0 - 4.0 * u1 + u2)
 
 
-def tangential(Uline: np.ndarray) -> np.ndarray:
-    """d/d(index) along a line of nodes (m, 4): central inside, one-sided at the two ends."""
+def tangential(Uline: np.ndarray, periodic: bool = False) -> np.ndarray:
+    """d/d(index) along a line of nodes (m, 4): central inside, one-sided at the two ends, or
+    central everywhere with wrap-around when the line is periodic."""
+    if periodic:
+        return 0.5 * (np.roll(Uline, -1, axis=0) - np.roll(Uline, 1, axis=0))
     d = np.zeros_like(Uline)
     d[1:-1] = 0.5 * (Uline[2:] - Uline[:-2])
     d[0] = -one_sided(Uline[0], Uline[1], Uline[2])

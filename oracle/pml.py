@@ -1,10 +1,19 @@
 """Perfectly matched layer of Sec. 3.
 
-Geometry (Fig. 2): the bulk B of nx x ny nodes is padded by W PML layers on every side; the
-fluid region F = B + P has Lx x Ly = (nx + 2W) x (ny + 2W) nodes. The PML layer index of a node
-is i = 1 .. W counted outward from the bulk (Eq. PML_ramp). Reading for the corner regions,
-where a node is outside the bulk along both axes: i = max(i_x, i_y) (Chebyshev distance from
-the bulk). Exponent: Eq. (PML_ramp) uses p = 2; the profile exponent is a parameter p.
+Geometry (Fig. 2): the bulk B of nx x ny nodes is padded by PML layers; the fluid region
+F = B + P has Lx x Ly nodes. Widths are per edge, (W_w, W_e, W_s, W_n), so that the damping
+zones away from the outlet can be thinner (the closing remark of Sec. 5); equal widths W on
+every side are the paper's setting, Lx x Ly = (nx + 2W) x (ny + 2W). The PML layer index of a
+node along an axis is i = 1 .. W_side counted outward from the bulk (Eq. PML_ramp), and its
+layer fraction along that axis is i / W_side.
+
+Absorption coefficients. Eq. (pml-general) has sigma_x and sigma_y; the paper then sets
+sigma_x = sigma_y = sigma (Eq. PMLCOLL). Default ("isotropic") reading: sigma_x = sigma_y =
+sigma_max f^p with f = max(f_x, f_y) the larger layer fraction (with equal widths this is the
+Chebyshev distance from the bulk, i = max(i_x, i_y), in the corners). Option "split": the
+general form with sigma_x = sigma_max f_x^p and sigma_y = sigma_max f_y^p (each nonzero only
+in the slab of its own axis; both in the corners). Exponent: Eq. (PML_ramp) uses p = 2; the
+profile exponent is a parameter p.
 
 Auxiliary variable Q, Eq. (PMLQ) dQ/dt = f_hat with the trapezoidal rule. The printed discrete
 rule lacks the previous value of Q; reading: Q^n = Q^(n-1) + (f_hat^(n-1) + f_hat^n) / 2 with
@@ -17,55 +26,96 @@ Gradient: Eq. (FD-dx-center) everywhere except along an axis whose outward neigh
 outside F (outermost layer), where Eq. (FD-dx-bw) is used along the outward normal n:
 dQ/dn = (3 Q(x) - 4 Q(x - n) + Q(x - 2n)) / 2, dQ/dx_a = n_a dQ/dn.
 
-Collision term, Eq. (PMLCOLL) with sigma_x = sigma_y = sigma:
-Omega^PML_i = -sigma (c_i . grad Q_i + 2 f_hat_i + sigma Q_i), with c_i the integer lattice
-velocity e_i (the discrete equation is written with dx = dt = 1), sigma per time step.
+Collision term, Eq. (pml-general):
+Omega^PML_i = -(sigma_y c_ix dQ_i/dx + sigma_x c_iy dQ_i/dy + (sigma_x + sigma_y) f_hat_i
+               + sigma_x sigma_y Q_i),
+which for sigma_x = sigma_y = sigma is Eq. (PMLCOLL), -sigma (c_i . grad Q_i + 2 f_hat_i +
+sigma Q_i); c_i is the integer lattice velocity e_i (the discrete equation is written with
+dx = dt = 1), sigma per time step.
 """
 from __future__ import annotations
 
 import numpy as np
 
 
-def _axis_layers(L, W):
-    """PML layer index along one axis: W - (distance to the nearer end), 0 outside the PML."""
-    if W == 0:
-        return np.zeros(L, dtype=np.int64)
-    z = np.arange(L)
-    return np.maximum(0, np.maximum(W - z, z - (L - 1 - W)))
-
-
-def layer_index(Lx: int, Ly: int, W: int, Wy: int = None) -> np.ndarray:
-    """(Ly, Lx) int array: PML layer index i in 1..W on P, 0 in the bulk (equal widths)."""
+def widths4(W, Wy=None):
+    """(W_w, W_e, W_s, W_n) from an int W (all edges, or the W/E edges when Wy is given) or
+    a 4-tuple."""
+    if np.ndim(W) == 1:
+        if Wy is not None:
+            raise ValueError("give either per-edge widths or W and Wy")
+        w = tuple(int(v) for v in W)
+        if len(w) != 4:
+            raise ValueError("per-edge widths are (W_w, W_e, W_s, W_n)")
+        return w
     Wy = W if Wy is None else Wy
-    return np.maximum(_axis_layers(Lx, W)[None, :], _axis_layers(Ly, Wy)[:, None])
+    return (int(W), int(W), int(Wy), int(Wy))
+
+
+def _axis_layers(L, lo, hi):
+    """(layer index, layer fraction) along one axis with lo layers at its start and hi at its
+    end: i = lo - z on the low side, z - (L - 1 - hi) on the high side, 0 in between."""
+    z = np.arange(L)
+    i_lo = np.maximum(0, lo - z) if lo > 0 else np.zeros(L, dtype=np.int64)
+    i_hi = np.maximum(0, z - (L - 1 - hi)) if hi > 0 else np.zeros(L, dtype=np.int64)
+    frac = np.zeros(L)
+    if lo > 0:
+        frac = np.where(i_lo > 0, i_lo / lo, frac)
+    if hi > 0:
+        frac = np.where(i_hi > 0, i_hi / hi, frac)
+    return i_lo + i_hi, frac
+
+
+def layer_index(Lx: int, Ly: int, W, Wy=None) -> np.ndarray:
+    """(Ly, Lx) int array: max(i_x, i_y) on P, 0 in the bulk."""
+    ww, we, ws, wn = widths4(W, Wy)
+    ix, _ = _axis_layers(Lx, ww, we)
+    iy, _ = _axis_layers(Ly, ws, wn)
+    return np.maximum(ix[None, :], iy[:, None])
+
+
+def sigma_fields(Lx, Ly, W, sigma_max, power, Wy=None, split=False):
+    """(sigma_x, sigma_y), each (Ly, Lx): Eq. (PML_ramp) with the reading of the module
+    docstring ("isotropic": both equal sigma_max max(f_x, f_y)^p; "split": per axis)."""
+    ww, we, ws, wn = widths4(W, Wy)
+    _, fx = _axis_layers(Lx, ww, we)
+    _, fy = _axis_layers(Ly, ws, wn)
+    FX = np.broadcast_to(fx[None, :], (Ly, Lx))
+    FY = np.broadcast_to(fy[:, None], (Ly, Lx))
+    if split:
+        return (np.where(FX > 0, sigma_max * FX ** power, 0.0),
+                np.where(FY > 0, sigma_max * FY ** power, 0.0))
+    f = np.maximum(FX, FY)
+    s = np.where(f > 0, sigma_max * f ** power, 0.0)
+    return s, s.copy()
 
 
 def sigma_field(Lx, Ly, W, sigma_max, power, Wy=None):
-    """Eq. (PML_ramp): sigma = sigma_max (i / W)^p on P, 0 in the bulk. With different widths
-    on the x edges (W) and y edges (Wy) the layer fraction is max(i_x / W, i_y / Wy)."""
-    Wy = W if Wy is None else Wy
-    fx = _axis_layers(Lx, W) / W if W > 0 else np.zeros(Lx)
-    fy = _axis_layers(Ly, Wy) / Wy if Wy > 0 else np.zeros(Ly)
-    frac = np.maximum(fx[None, :], fy[:, None])
-    return np.where(frac > 0, sigma_max * frac ** power, 0.0)
+    """Eq. (PML_ramp) with sigma_x = sigma_y: sigma_max max(f_x, f_y)^p on P, 0 in the bulk."""
+    return sigma_fields(Lx, Ly, W, sigma_max, power, Wy)[0]
 
 
 def in_pml(Lx, Ly, W, Wy=None) -> np.ndarray:
     """Nodes of P (PML layer index >= 1 along some axis)."""
-    Wy = W if Wy is None else Wy
-    return (_axis_layers(Lx, W)[None, :] > 0) | (_axis_layers(Ly, Wy)[:, None] > 0)
+    return layer_index(Lx, Ly, W, Wy) > 0
 
 
 def q_support(Lx, Ly, W, Wy=None) -> np.ndarray:
-    """Nodes where Q is kept: P plus the bulk nodes one step inside it along each PML axis (the
+    """Nodes where Q is kept: P plus the bulk nodes one step inside it along each PML edge (the
     ring the central difference of the innermost layer reaches)."""
-    Wy = W if Wy is None else Wy
+    ww, we, ws, wn = widths4(W, Wy)
     x = np.arange(Lx)
     y = np.arange(Ly)
-    dx = np.minimum(x, Lx - 1 - x)
-    dy = np.minimum(y, Ly - 1 - y)
-    sx = (dx <= W) if W > 0 else np.zeros(Lx, dtype=bool)
-    sy = (dy <= Wy) if Wy > 0 else np.zeros(Ly, dtype=bool)
+    sx = np.zeros(Lx, dtype=bool)
+    sy = np.zeros(Ly, dtype=bool)
+    if ww > 0:
+        sx |= x <= ww
+    if we > 0:
+        sx |= Lx - 1 - x <= we
+    if ws > 0:
+        sy |= y <= ws
+    if wn > 0:
+        sy |= Ly - 1 - y <= wn
     return sx[None, :] | sy[:, None]
 
 
@@ -96,8 +146,12 @@ def gradient(Q: np.ndarray, periodic_y: bool = False):
     return gx, gy
 
 
-def omega_pml(e: np.ndarray, gx, gy, fhat, Q, sigma):
-    """Eq. (PMLCOLL): -sigma (c_i . grad Q_i + 2 f_hat_i + sigma Q_i), shape (q, Ly, Lx)."""
+def omega_pml(e: np.ndarray, gx, gy, fhat, Q, sigma_x, sigma_y=None):
+    """Eq. (pml-general), shape (q, Ly, Lx):
+    -(sigma_y c_x dQ/dx + sigma_x c_y dQ/dy + (sigma_x + sigma_y) f_hat + sigma_x sigma_y Q);
+    sigma_y defaults to sigma_x (Eq. PMLCOLL)."""
+    sigma_y = sigma_x if sigma_y is None else sigma_y
     ex = e[:, 0].astype(np.float64).reshape(-1, 1, 1)
     ey = e[:, 1].astype(np.float64).reshape(-1, 1, 1)
-    return -sigma * (ex * gx + ey * gy + 2.0 * fhat + sigma * Q)
+    return -(sigma_y * ex * gx + sigma_x * ey * gy + (sigma_x + sigma_y) * fhat
+             + sigma_x * sigma_y * Q)

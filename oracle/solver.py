@@ -1,6 +1,7 @@
 """One time step of the PML + outer-BC lattice Boltzmann scheme, written out literally.
 
-Grid. Bulk nx x ny; fluid region F = bulk + W PML layers per side (Lx x Ly); boundary band
+Grid. Bulk nx x ny; fluid region F = bulk + PML layers (W per side, or per-edge widths;
+Lx x Ly); boundary band
 Gamma = M layers outside F (M = maximum displacement of the stencil, 3 for D2Q37), so every
 pull source x - e_i of a node of F lies on the allocated grid G = F + Gamma. Reading of the
 boundary nodes x_(b,j), j = 1..M, of Sec. 4: they are the nodes of Gamma; after streaming
@@ -40,37 +41,38 @@ EDGES = ("W", "E", "S", "N")
 class OracleLBM:
     def __init__(self, nx, ny, W, tau, sigma_max=0.0, sigma_power=2, bc="zg", q=37,
                  nrbc_edges=(0, 0, 0, 0), beta=0.0, mean=(1.0, 0.0, 0.0, 1.0),
-                 relax_sign=-1.0, pml_on=True, Wy=None, periodic_y=False):
-        """W: PML layers on the x edges (and on the y edges unless Wy is given). periodic_y:
-        the y axis wraps (no PML on it: Wy defaults to, and must be, 0); the x edges keep the
-        chosen BC."""
+                 relax_sign=-1.0, pml_on=True, Wy=None, periodic_y=False, sigma_split=False):
+        """W: PML layers on every edge, or on the W and E edges when Wy (S and N edges) is
+        given, or a per-edge tuple (W_w, W_e, W_s, W_n). periodic_y: the y axis wraps (no PML
+        on it; Wy defaults to 0 then); the x edges keep the chosen BC. sigma_split: the
+        general sigma_x != sigma_y form of Eq. (pml-general) instead of sigma_x = sigma_y."""
         self.lat = lattice(q)
         self.pml_on = pml_on
         self.periodic_y = bool(periodic_y)
-        self.Wy = (0 if self.periodic_y else W) if Wy is None else Wy
-        if self.periodic_y and (self.Wy != 0 or bc == "periodic"):
-            raise ValueError("a periodic y axis has no PML (Wy = 0) and needs a zg/nrbc x edge")
-        if self.periodic_y and bc == "nrbc" and (nrbc_edges[0] or nrbc_edges[1]):
-            raise ValueError("CBC relax on an edge whose tangent is periodic is not supported")
-        if self.Wy == 1:
+        if self.periodic_y and Wy is None and np.ndim(W) == 0:
+            Wy = 0
+        self.widths = pml.widths4(W, Wy)
+        ww, we, ws, wn = self.widths
+        if any(w < 0 or w == 1 for w in self.widths):
             raise ValueError("a PML needs W >= 2 (one-sided difference reaches 2 nodes in)")
-        self.nx, self.ny, self.W = nx, ny, W
-        self.Lx, self.Ly = nx + 2 * W, ny + 2 * self.Wy
+        if bc == "periodic" and any(self.widths):
+            raise ValueError("periodic mode has no PML")
+        if self.periodic_y and (ws or wn or bc == "periodic"):
+            raise ValueError("a periodic y axis has no PML and needs a zg/nrbc x edge")
+        self.nx, self.ny = nx, ny
+        self.Lx, self.Ly = nx + ww + we, ny + ws + wn
         self.M = self.lat.M
         self.tau = tau
         self.bc = bc
         self.nrbc_edges = tuple(nrbc_edges)
         self.beta = beta
         self.relax_sign = relax_sign
-        if bc == "periodic" and W != 0:
-            raise ValueError("periodic mode has no PML")
-        if W == 1:
-            raise ValueError("a PML needs W >= 2 (one-sided difference reaches 2 nodes in)")
         M, Lx, Ly = self.M, self.Lx, self.Ly
         self.Gx, self.Gy = Lx + 2 * M, Ly + 2 * M
-        self.sigma = pml.sigma_field(Lx, Ly, W, sigma_max, sigma_power, self.Wy)
-        self.in_P = pml.in_pml(Lx, Ly, W, self.Wy)
-        self.qsup = pml.q_support(Lx, Ly, W, self.Wy)
+        self.sigma_x, self.sigma_y = pml.sigma_fields(Lx, Ly, self.widths, sigma_max,
+                                                      sigma_power, split=sigma_split)
+        self.in_P = pml.in_pml(Lx, Ly, self.widths)
+        self.qsup = pml.q_support(Lx, Ly, self.widths)
         self.edges = ("W", "E") if self.periodic_y else EDGES
         rho0, u0x, u0y, T0 = mean
         self.fbar = feq(np.float64(rho0), np.array([u0x, u0y]), np.float64(T0),
@@ -156,7 +158,7 @@ class OracleLBM:
 
                 U0 = V[edge][j - 1]
                 dUn = out * ch.one_sided(U0, U_at(j - 1), U_at(j - 2))
-                dUt = ch.tangential(U0)
+                dUt = ch.tangential(U0, periodic=self.periodic_y and axis == 0)
                 layers.append(ch.rate(U0, dUn, dUt, axis, out, self.nrbc_edges[k], self.beta,
                                       self.lat.r, self.relax_sign))
             rates[edge] = layers
@@ -208,7 +210,7 @@ class OracleLBM:
             rho, u, T = moments(f, lat.xi)                                   # 1
             fe = self._feq(rho, u, T)                                        # 2
             fstar = bgk(f, fe, self.tau)                                     # 5 (BGK part)
-            if (self.W > 0 or self.Wy > 0) and self.pml_on:
+            if any(self.widths) and self.pml_on:
                 Fs = self.Fs
                 fhat = np.where(self.qsup, fe[Fs] - self.fbar[:, None, None], 0.0)   # 3
                 if self.Q is None:
@@ -218,7 +220,7 @@ class OracleLBM:
                                  0.0)
                 self.Q, self.fhat_prev = Q, fhat
                 gx, gy = pml.gradient(Q, self.periodic_y)                    # 4
-                om = pml.omega_pml(lat.e, gx, gy, fhat, Q, self.sigma)
+                om = pml.omega_pml(lat.e, gx, gy, fhat, Q, self.sigma_x, self.sigma_y)
                 fstar[Fs] = fstar[Fs] + np.where(self.in_P, om, 0.0)         # 5 (PML part)
             if self.periodic_y:
                 # the rows beyond a periodic y axis carry the post-collision populations of
@@ -241,8 +243,8 @@ class OracleLBM:
         rho, u, T = moments(self.f[self.Fs], self.lat.xi)
         out = (rho, u[0], u[1], T)
         if region == "bulk":
-            W, Wy = self.W, self.Wy
-            out = tuple(a[Wy:Wy + self.ny, W:W + self.nx] for a in out)
+            ww, ws = self.widths[0], self.widths[2]
+            out = tuple(a[ws:ws + self.ny, ww:ww + self.nx] for a in out)
         return out
 
     def totals(self):

@@ -25,13 +25,14 @@ class lbm_grid(C.Structure):
 
 
 class lbm_sigma_profile(C.Structure):
-    _fields_ = [("sigma_max", C.c_double), ("power", C.c_int)]
+    _fields_ = [("sigma_max", C.c_double), ("power", C.c_int), ("split", C.c_int)]
 
 
 class lbm_bc_params(C.Structure):
     _fields_ = [("edge", C.c_int * 4), ("beta", C.c_double), ("relax_sign", C.c_double),
                 ("rho0", C.c_double), ("u0x", C.c_double), ("u0y", C.c_double),
-                ("T0", C.c_double), ("pml_width_y", C.c_int), ("periodic_y", C.c_int)]
+                ("T0", C.c_double), ("use_pml_widths", C.c_int), ("pml_widths", C.c_int * 4),
+                ("periodic_y", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)

@@ -267,23 +267,28 @@ lbm_status lbm_lattice_info(lbm_stencil stencil, int* q, int* e, double* w, doub
 }
 
 // Storage geometry of a grid (section "Storage" of lbm_device.cuh) and the bytes it needs.
-static Geom make_geom(int nx, int ny, int W, int M, int Wy, int py) {
+static Geom make_geom(int nx, int ny, const int W[4], int M, int py) {
   Geom g{};
   g.nx = nx;
   g.ny = ny;
-  g.W = W;
-  g.Wy = Wy;
+  g.Ww = W[0];
+  g.We = W[1];
+  g.Ws = W[2];
+  g.Wn = W[3];
   g.py = py;
   g.M = M;
-  g.Lx = nx + 2 * W;
-  g.Ly = ny + 2 * Wy;
+  g.Lx = nx + g.Ww + g.We;
+  g.Ly = ny + g.Ws + g.Wn;
   g.cF0 = 32;
   g.pitch = ((g.cF0 + g.Lx + g.M) + 31) / 32 * 32;
   g.plane = ((long long)g.pitch * (g.Ly + 2 * g.M) + 63) / 64 * 64;
-  g.Wf = g.W > 0 ? std::max(g.W + 1, g.M) : g.M;
-  g.Wfy = py ? 0 : (g.Wy > 0 ? std::max(g.Wy + 1, g.M) : g.M);
-  g.frame_n = 2 * g.Wfy * g.Lx + 2 * (g.Ly - 2 * g.Wfy) * g.Wf;
-  g.Sp = (g.W > 0 || g.Wy > 0) ? ((long long)g.frame_n + 31) / 32 * 32 : 0;
+  auto depth = [&](int w) { return w > 0 ? std::max(w + 1, g.M) : g.M; };
+  g.Fw = depth(g.Ww);
+  g.Fe = depth(g.We);
+  g.Fs = py ? 0 : depth(g.Ws);
+  g.Fn = py ? 0 : depth(g.Wn);
+  g.frame_n = (g.Fs + g.Fn) * g.Lx + (g.Ly - g.Fs - g.Fn) * (g.Fw + g.Fe);
+  g.Sp = has_pml(g) ? ((long long)g.frame_n + 31) / 32 * 32 : 0;
   g.nb = 2 * g.M * (g.Lx + g.Ly);
   g.ne = 4 * (g.Lx + g.Ly);
   g.ngamma = 2 * g.M * (g.Lx + 2 * g.M) + 2 * g.M * g.Ly;
@@ -305,7 +310,8 @@ extern "C" lbm_status lbm_estimate_bytes(const lbm_grid* grid, lbm_stencil stenc
       pml_width == 1 || (bc == LBM_BC_PERIODIC && pml_width != 0) ||
       (precision != LBM_FP64 && precision != LBM_FP32_DEV))
     return LBM_EINVAL;
-  const Geom g = make_geom(grid->nx, grid->ny, pml_width, halo_of(q), pml_width, 0);
+  const int W4[4] = {pml_width, pml_width, pml_width, pml_width};
+  const Geom g = make_geom(grid->nx, grid->ny, W4, halo_of(q), 0);
   *bytes = bytes_of(g, q, precision == LBM_FP64 ? 8 : 4);
   return LBM_OK;
 }
@@ -321,24 +327,28 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   if (q != 37 && q != 17 && q != 9) return fail("stencil must be 9, 17 or 37");
   if (grid->nx < 8 || grid->ny < 8) return fail("bulk must be at least 8 x 8");
   if (!(tau > 0.5)) return fail("tau must exceed 1/2");
-  if (pml_width < 0 || pml_width == 1) return fail("pml_width must be 0 or >= 2");
+  if (pml_width < 0 || pml_width == 1 || pml_width > 4096)
+    return fail("pml_width must be 0 or 2..4096");
   if (bc != LBM_BC_PERIODIC && bc != LBM_BC_ZG && bc != LBM_BC_NRBC) return fail("bad bc kind");
-  if (bc == LBM_BC_PERIODIC && pml_width != 0) return fail("periodic mode has no PML");
   if (precision != LBM_FP64 && precision != LBM_FP32_DEV) return fail("bad precision");
-  lbm_sigma_profile sg = sigma ? *sigma : lbm_sigma_profile{0.0, 2};
-  if (!(sg.sigma_max >= 0.0) || !std::isfinite(sg.sigma_max) || sg.power < 0 || sg.power > 16)
+  lbm_sigma_profile sg = sigma ? *sigma : lbm_sigma_profile{0.0, 2, 0};
+  if (!(sg.sigma_max >= 0.0) || !std::isfinite(sg.sigma_max) || sg.power < 0 || sg.power > 16 ||
+      (sg.split != 0 && sg.split != 1))
     return fail("bad sigma profile");
   lbm_bc_params bp;
   if (bcp) bp = *bcp;
-  else { std::memset(&bp, 0, sizeof bp); bp.rho0 = 1.0; bp.T0 = 1.0; bp.pml_width_y = -1; }
+  else { std::memset(&bp, 0, sizeof bp); bp.rho0 = 1.0; bp.T0 = 1.0; }
   if (bp.periodic_y != 0 && bp.periodic_y != 1) return fail("periodic_y must be 0 or 1");
-  const int Wy = bp.periodic_y ? 0 : (bp.pml_width_y < 0 ? pml_width : bp.pml_width_y);
-  if (bp.periodic_y && bp.pml_width_y > 0) return fail("a periodic y axis has no PML");
+  if (bp.use_pml_widths != 0 && bp.use_pml_widths != 1) return fail("use_pml_widths must be 0 or 1");
+  int W4[4];
+  for (int k = 0; k < 4; ++k) W4[k] = bp.use_pml_widths ? bp.pml_widths[k] : pml_width;
+  if (bp.periodic_y && !bp.use_pml_widths) W4[2] = W4[3] = 0;
+  for (int k = 0; k < 4; ++k)
+    if (W4[k] < 0 || W4[k] == 1 || W4[k] > 4096) return fail("PML widths must be 0 or 2..4096");
+  if (bc == LBM_BC_PERIODIC && (W4[0] | W4[1] | W4[2] | W4[3]))
+    return fail("periodic mode has no PML");
+  if (bp.periodic_y && (W4[2] || W4[3])) return fail("a periodic y axis has no PML");
   if (bp.periodic_y && bc == LBM_BC_PERIODIC) return fail("periodic_y needs a ZG or NRBC x edge");
-  if (bp.periodic_y && bc == LBM_BC_NRBC && (bp.edge[0] != 0 || bp.edge[1] != 0))
-    return fail("with periodic_y the W and E edges must be PNR_LODI");
-  if (Wy == 1) return fail("pml_width_y must be 0 or >= 2");
-  if (grid->ny < 8 || grid->nx < 8) return fail("bulk must be at least 8 x 8");
   if (!(bp.rho0 > 0) || !(bp.T0 > 0) || !std::isfinite(bp.u0x) || !std::isfinite(bp.u0y) ||
       !std::isfinite(bp.beta))
     return fail("bad mean state or beta");
@@ -359,7 +369,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   if (!lattice_of(q, ctx->w, &ctx->r, lerr)) { delete ctx; return fail("quadrature failed"); }
   cudaGetDevice(&ctx->device);
 
-  ctx->g = make_geom(grid->nx, grid->ny, pml_width, halo_of(q), Wy, bp.periodic_y);
+  ctx->g = make_geom(grid->nx, grid->ny, W4, halo_of(q), bp.periodic_y);
   Geom& g = ctx->g;
 
   switch (q * 2 + (precision == LBM_FP32_DEV)) {
@@ -385,7 +395,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   for (int k = 0; k < 2; ++k) {
     if (cudaMalloc(&ctx->f[k], ctx->fbytes) != cudaSuccess) return oom("populations");
     if (cudaMemset(ctx->f[k], 0, ctx->fbytes) != cudaSuccess) return oom("populations");
-    if (g.W > 0 || g.Wy > 0) {
+    if (has_pml(g)) {
       if (cudaMalloc(&ctx->S[k], ctx->sbytes) != cudaSuccess) return oom("PML accumulator");
       if (cudaMemset(ctx->S[k], 0, ctx->sbytes) != cudaSuccess) return oom("PML accumulator");
     }
@@ -448,9 +458,9 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
     d.cf.eqbar[i] = (float)(fbar[i] - ctx->w[i]);
   }
   d.cd.r = ctx->r; d.cd.r2 = ctx->r * ctx->r; d.cd.omega = ctx->omega;
-  d.cd.sigma_max = sg.sigma_max; d.cd.power = sg.power;
+  d.cd.sigma_max = sg.sigma_max; d.cd.power = sg.power; d.cd.split = sg.split;
   d.cf.r = (float)ctx->r; d.cf.r2 = (float)(ctx->r * ctx->r); d.cf.omega = (float)ctx->omega;
-  d.cf.sigma_max = (float)sg.sigma_max; d.cf.power = sg.power;
+  d.cf.sigma_max = (float)sg.sigma_max; d.cf.power = sg.power; d.cf.split = sg.split;
   if (ctx->ops.prepare() != cudaSuccess) return oom("kernel attributes");
   if (cudaDeviceSynchronize() != cudaSuccess) return oom("device sync");
   *out = ctx;
@@ -471,8 +481,9 @@ const char* lbm_last_error(const lbm_ctx* ctx) {
 lbm_status lbm_geometry(const lbm_ctx* ctx, int64_t* out) {
   if (!ctx || !out) return LBM_EINVAL;
   const Geom& g = ctx->g;
-  out[0] = g.nx; out[1] = g.ny; out[2] = g.W; out[3] = g.M;
+  out[0] = g.nx; out[1] = g.ny; out[2] = g.Ww; out[3] = g.M;
   out[4] = g.Lx; out[5] = g.Ly; out[6] = ctx->q; out[7] = ctx->steps;
+  out[8] = g.Ww; out[9] = g.We; out[10] = g.Ws; out[11] = g.Wn;
   return LBM_OK;
 }
 
@@ -715,7 +726,13 @@ lbm_status lbm_profile_read(lbm_ctx* ctx, double* ms, int* steps) {
 
 // checkpoint layout: header of 8 int64, then current and previous population buffers, the PML
 // accumulator of the current level, the targets and the saved edge moments
-struct CkptHeader { int64_t magic, q, nx, ny, W, prec, steps, flags; };
+struct CkptHeader { int64_t magic, q, nx, ny, widths, prec, steps, flags; };
+
+// the four PML widths (each <= 4096) packed 16 bits apiece, and the sigma form
+static int64_t pack_widths(const lbm_ctx* ctx) {
+  const Geom& g = ctx->g;
+  return (int64_t)g.Ww | ((int64_t)g.We << 16) | ((int64_t)g.Ws << 32) | ((int64_t)g.Wn << 48);
+}
 static const int64_t kMagic = 0x4c424d434b505431ll;
 
 lbm_status lbm_checkpoint_size(const lbm_ctx* ctx, size_t* bytes) {
@@ -732,9 +749,10 @@ lbm_status lbm_checkpoint(lbm_ctx* ctx, void* host, size_t bytes) {
   lbm_checkpoint_size(ctx, &need);
   if (!host || bytes < need) { ctx->err = "checkpoint buffer too small"; return LBM_EINVAL; }
   char* p = static_cast<char*>(host);
-  CkptHeader h{kMagic, ctx->q, ctx->g.nx, ctx->g.ny, ctx->g.W, (int64_t)ctx->prec, ctx->steps,
+  CkptHeader h{kMagic, ctx->q, ctx->g.nx, ctx->g.ny, pack_widths(ctx), (int64_t)ctx->prec,
+               ctx->steps,
                (int64_t)(ctx->prev_valid ? 1 : 0) | (int64_t)(ctx->prev_prestream ? 2 : 0) |
-                   ((int64_t)ctx->g.py << 2) | ((int64_t)ctx->g.Wy << 8)};
+                   ((int64_t)ctx->g.py << 2)};
   std::memcpy(p, &h, sizeof h);
   p += sizeof h;
   const cudaMemcpyKind k = cudaMemcpyDeviceToHost;
@@ -757,8 +775,8 @@ lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes) {
   CkptHeader h;
   std::memcpy(&h, p, sizeof h);
   if (h.magic != kMagic || h.q != ctx->q || h.nx != ctx->g.nx || h.ny != ctx->g.ny ||
-      h.W != ctx->g.W || h.prec != (int64_t)ctx->prec || ((h.flags >> 2) & 1) != ctx->g.py ||
-      (h.flags >> 8) != ctx->g.Wy) {
+      h.widths != pack_widths(ctx) || h.prec != (int64_t)ctx->prec ||
+      ((h.flags >> 2) & 1) != ctx->g.py) {
     ctx->err = "checkpoint does not match this context";
     return LBM_EINVAL;
   }

@@ -11,8 +11,9 @@
 //
 // Work split of one step (all kernels read buffer A and write disjoint parts of buffer B):
 //   k_nrbc_stage x4   characteristic targets U_tgt^(n+1) on the edge bands (Sec. 4)
-//   k_bulk            nodes of F at distance >= Wf from the outer edge: BGK only
-//   k_frame1          the frame (distance < Wf): BGK, PML accumulator, local PML terms,
+//   k_bulk            nodes of F inside the frame depths (Fw, Fe, Fs, Fn): BGK only
+//   k_frame1          the frame (the outer Fw / Fe / Fs / Fn layers of F): BGK, PML
+//                     accumulator, local PML terms,
 //                     saving the outer two layers' moments for the characteristic BC
 //   k_frame2          PML nodes: the gradient part of Omega^PML (needs the frame's new Q)
 //   k_gamma           the M boundary layers outside F (zero gradient, characteristic BC with
@@ -30,20 +31,22 @@ namespace lbm {
 constexpr int kMaxQ = 37;
 
 struct Geom {
-  int nx, ny, W, M, Lx, Ly;
-  int Wy;            // PML layers on the S and N edges (W: on the W and E edges)
-  int py;            // 1: the y axis is periodic (then Wy = 0)
+  int nx, ny, M, Lx, Ly;
+  int Ww, We, Ws, Wn; // PML layers on the W, E, S and N edges (0: none there)
+  int py;            // 1: the y axis is periodic (then Ws = Wn = 0)
   int pitch;         // storage row length (elements), multiple of 32
   int cF0;           // storage column of x = 0 of F, multiple of 32
   long long plane;   // elements per direction plane (pitch * (Ly + 2M))
-  int Wf;            // frame depth along x: max(W + 1, M) when W > 0, else M
-  int Wfy;           // frame depth along y: likewise with Wy; 0 on a periodic y axis
+  int Fw, Fe, Fs, Fn; // frame depth per edge: max(W_edge + 1, M) with a PML there, else M;
+                     // Fs = Fn = 0 on a periodic y axis
   int frame_n;       // number of frame nodes
   long long Sp;      // PML accumulator stride per direction
   int nb;            // characteristic-BC band nodes: 2 M (Lx + Ly)
   int ne;            // saved fluid-moment slots: 4 (Lx + Ly) (two layers per edge)
   int ngamma;        // boundary nodes outside F: 2M(Lx + 2M) + 2M Ly
 };
+
+__host__ __device__ inline bool has_pml(const Geom& g) { return (g.Ww | g.We | g.Ws | g.Wn) > 0; }
 
 // Lattice and physics constants in the arithmetic type of a kernel. eqbar holds the
 // equilibrium of the PML mean state (Eq. decomp-NJ) in the storage representation.
@@ -53,6 +56,7 @@ struct Consts {
   Real eqbar[kMaxQ];
   Real r, r2, omega, sigma_max;
   int power;
+  int split;         // 1: sigma_x != sigma_y (Eq. pml-general), 0: sigma_x = sigma_y (Eq. PMLCOLL)
 };
 
 struct BcParams {
@@ -69,53 +73,55 @@ __device__ inline int dist_out(const Geom& g, int x, int y) {
   return min(min(x, g.Lx - 1 - x), min(y, g.Ly - 1 - y));
 }
 
-// PML classification of node (x, y) of F: layer index per axis i_x = W - (distance to the
-// nearer x edge) (0 outside the x PML), likewise i_y with Wy; P = {i_x > 0 or i_y > 0}; the
-// accumulator Q is kept on P and on the ring one node inside it along each PML axis. Layer
-// fraction max(i_x / W, i_y / Wy) (Chebyshev in corners; Eq. PML_ramp's i / W for equal widths).
+// PML classification of node (x, y) of F. Layer index along x: i = W_w - x near the W edge,
+// x - (Lx - 1 - W_e) near the E edge, 0 between (likewise along y with W_s, W_n); layer
+// fraction f_x = i / (width of that edge). P = {f_x > 0 or f_y > 0}; the accumulator Q is kept
+// on P and on the ring one node inside each PML edge.
 template <class Real>
 struct PmlNode {
   bool has_q, in_p;
-  Real frac;
+  Real fx, fy;
 };
 
 template <class Real>
 __device__ inline PmlNode<Real> pml_node(const Geom& g, int x, int y) {
-  const int dx = min(x, g.Lx - 1 - x), dy = min(y, g.Ly - 1 - y);
-  const int ix = g.W > 0 ? max(0, g.W - dx) : 0;
-  const int iy = g.Wy > 0 ? max(0, g.Wy - dy) : 0;
+  const int ex = g.Lx - 1 - x, ey = g.Ly - 1 - y;
+  const int iw = g.Ww > 0 ? max(0, g.Ww - x) : 0, ie = g.We > 0 ? max(0, g.We - ex) : 0;
+  const int is = g.Ws > 0 ? max(0, g.Ws - y) : 0, in = g.Wn > 0 ? max(0, g.Wn - ey) : 0;
   PmlNode<Real> n;
-  n.in_p = ix > 0 || iy > 0;
-  n.has_q = (g.W > 0 && dx <= g.W) || (g.Wy > 0 && dy <= g.Wy);
-  const Real fx = g.W > 0 ? Real(ix) / Real(g.W) : Real(0);
-  const Real fy = g.Wy > 0 ? Real(iy) / Real(g.Wy) : Real(0);
-  n.frac = fx > fy ? fx : fy;
+  n.in_p = (iw | ie | is | in) > 0;
+  n.has_q = (g.Ww > 0 && x <= g.Ww) || (g.We > 0 && ex <= g.We) || (g.Ws > 0 && y <= g.Ws) ||
+            (g.Wn > 0 && ey <= g.Wn);
+  n.fx = iw > 0 ? Real(iw) / Real(g.Ww) : (ie > 0 ? Real(ie) / Real(g.We) : Real(0));
+  n.fy = is > 0 ? Real(is) / Real(g.Ws) : (in > 0 ? Real(in) / Real(g.Wn) : Real(0));
   return n;
 }
 
-// Frame: bottom rows (Wfy), top rows (Wfy), then left and right columns (Wf) of the middle rows.
+// Frame: bottom rows (Fs), top rows (Fn), then left (Fw) and right (Fe) columns of the
+// middle rows.
 __device__ inline void frame_xy(const Geom& g, int fi, int& x, int& y) {
-  const int Lx = g.Lx, Wf = g.Wf, Wfy = g.Wfy;
-  const int bot = Wfy * Lx;
+  const int Lx = g.Lx;
+  const int bot = g.Fs * Lx, top = g.Fn * Lx;
   if (fi < bot) { y = fi / Lx; x = fi - y * Lx; return; }
   fi -= bot;
-  if (fi < bot) { int t = fi / Lx; y = g.Ly - Wfy + t; x = fi - t * Lx; return; }
-  fi -= bot;
-  const int side = (g.Ly - 2 * Wfy) * Wf;
-  if (fi < side) { int t = fi / Wf; y = Wfy + t; x = fi - t * Wf; return; }
-  fi -= side;
-  int t = fi / Wf;
-  y = Wfy + t;
-  x = g.Lx - Wf + (fi - t * Wf);
+  if (fi < top) { int t = fi / Lx; y = g.Ly - g.Fn + t; x = fi - t * Lx; return; }
+  fi -= top;
+  const int mid = g.Ly - g.Fs - g.Fn;
+  const int left = mid * g.Fw;
+  if (fi < left) { int t = fi / g.Fw; y = g.Fs + t; x = fi - t * g.Fw; return; }
+  fi -= left;
+  int t = fi / g.Fe;
+  y = g.Fs + t;
+  x = g.Lx - g.Fe + (fi - t * g.Fe);
 }
 
 __device__ inline int frame_index(const Geom& g, int x, int y) {
-  const int Lx = g.Lx, Wf = g.Wf, Wfy = g.Wfy;
-  if (y < Wfy) return y * Lx + x;
-  if (y >= g.Ly - Wfy) return Wfy * Lx + (y - (g.Ly - Wfy)) * Lx + x;
-  const int base = 2 * Wfy * Lx;
-  if (x < Wf) return base + (y - Wfy) * Wf + x;
-  return base + (g.Ly - 2 * Wfy) * Wf + (y - Wfy) * Wf + (x - (g.Lx - Wf));
+  const int Lx = g.Lx;
+  if (y < g.Fs) return y * Lx + x;
+  if (y >= g.Ly - g.Fn) return g.Fs * Lx + (y - (g.Ly - g.Fn)) * Lx + x;
+  const int base = (g.Fs + g.Fn) * Lx;
+  if (x < g.Fw) return base + (y - g.Fs) * g.Fw + x;
+  return base + (g.Ly - g.Fs - g.Fn) * g.Fw + (y - g.Fs) * g.Fe + (x - (g.Lx - g.Fe));
 }
 
 // sigma of Eq. (PML_ramp) for layer fraction frac = i / W.
@@ -124,6 +130,20 @@ __device__ inline Real sigma_of(const Consts<Real>& c, Real frac) {
   Real p = Real(1);
   for (int k = 0; k < c.power; ++k) p *= frac;
   return c.sigma_max * p;
+}
+
+// (sigma_x, sigma_y) of a node of P: both sigma(max(f_x, f_y)) (Eq. PMLCOLL, corners by the
+// larger fraction), or per axis in the split form of Eq. (pml-general).
+template <class Real>
+__device__ inline void pml_sigmas(const Consts<Real>& c, const PmlNode<Real>& n, Real& sx,
+                                  Real& sy) {
+  if (c.split) {
+    sx = n.fx > Real(0) ? sigma_of(c, n.fx) : Real(0);
+    sy = n.fy > Real(0) ? sigma_of(c, n.fy) : Real(0);
+  } else {
+    sx = sigma_of(c, n.fx > n.fy ? n.fx : n.fy);
+    sy = sx;
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -306,15 +326,15 @@ __device__ inline void load_pop(Real (&p)[S::Q], const Real* __restrict__ A, con
 // Kernels
 // ------------------------------------------------------------------------------------------
 
-// Interior of F (distance >= Wf from its outer edge): pull, moments, BGK, store.
+// Interior of F (inside the frame depths Fw, Fe, Fs, Fn): pull, moments, BGK, store.
 // Block: 32 x BY threads; the x tiles start on a 32-node boundary of F.
 template <class S, class Real, bool DEV, bool STREAM>
 __global__ void __launch_bounds__(256) k_bulk(Geom g, Consts<Real> c, const Real* __restrict__ A,
                                               Real* __restrict__ B, int* flag) {
-  const int x0 = (g.Wf / 32) * 32;
+  const int x0 = (g.Fw / 32) * 32;
   const int x = x0 + blockIdx.x * 32 + threadIdx.x;
-  const int y = g.Wfy + blockIdx.y * blockDim.y + threadIdx.y;
-  if (x < g.Wf || x >= g.Lx - g.Wf || y >= g.Ly - g.Wfy) return;
+  const int y = g.Fs + blockIdx.y * blockDim.y + threadIdx.y;
+  if (x < g.Fw || x >= g.Lx - g.Fe || y >= g.Ly - g.Fn) return;
   const long long idx = gindex(g, x, y);
   Real p[S::Q];
   load_pop<S, Real, STREAM>(p, A, g, idx);
@@ -349,7 +369,8 @@ __device__ inline void save_edge_moments(const Geom& g, double* Ue, int x, int y
 
 // Frame, phase 1: BGK plus, on P and its inner ring, the trapezoidal accumulator
 // S = Q + f_hat / 2 (Eq. PMLQ: Q^n = S^(n-1) + f_hat^n / 2, S^n = S^(n-1) + f_hat^n), and on P
-// the local part -sigma (2 f_hat + sigma Q) of Eq. (PMLCOLL).
+// the local part -((sigma_x + sigma_y) f_hat + sigma_x sigma_y Q) of Eq. (pml-general)
+// (-sigma (2 f_hat + sigma Q) of Eq. PMLCOLL when sigma_x = sigma_y).
 template <class S, class Real, bool DEV, bool STREAM>
 __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Real* __restrict__ A,
                                                 Real* __restrict__ B, const Real* __restrict__ Sold,
@@ -369,7 +390,9 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
   const PmlNode<Real> pn = pml_node<Real>(g, x, y);
   const bool has_q = pn.has_q;
   const bool in_p = pn.in_p;
-  const Real sig = in_p ? sigma_of(c, pn.frac) : Real(0);
+  Real sx = Real(0), sy = Real(0);
+  if (in_p) pml_sigmas(c, pn, sx, sy);
+  const Real ssum = sx + sy, sprod = sx * sy;
   const EqCoef<Real> k = eq_coef<S::ORDER, Real>(m);
   if (has_q) {
     // all accumulator loads in flight before any store
@@ -383,7 +406,7 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
       const Real q = so[i] + Real(0.5) * fhat;
       Snew[(long long)i * g.Sp + fi] = so[i] + fhat;
       Real out = p[i] + c.omega * (eq - p[i]);
-      if (in_p) out = out - sig * (Real(2) * fhat + sig * q);
+      if (in_p) out = out - (ssum * fhat + sprod * q);
       B[(long long)i * g.plane + idx] = out;
     }
   } else {
@@ -393,7 +416,8 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
   }
 }
 
-// Frame, phase 2 (PML nodes): subtract sigma e_i . grad Q_i with Q = (S^(n-1) + S^n) / 2,
+// Frame, phase 2 (PML nodes): subtract sigma_y c_ix dQ_i/dx + sigma_x c_iy dQ_i/dy (sigma
+// e_i . grad Q_i when sigma_x = sigma_y) with Q = (S^(n-1) + S^n) / 2,
 // Eq. (FD-dx-center) per axis, Eq. (FD-dx-bw) along the outward normal at the outermost layer.
 template <class S, class Real>
 __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __restrict__ B,
@@ -405,7 +429,8 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
   frame_xy(g, fi, x, y);
   const PmlNode<Real> pn = pml_node<Real>(g, x, y);
   if (!pn.in_p) return;
-  const Real sig = sigma_of(c, pn.frac);
+  Real sx, sy;
+  pml_sigmas(c, pn, sx, sy);
   // x axis: neighbours / one-sided stencil
   int ax0, ax1, ax2;  // frame indices; derivative = cx0*Q(ax0) + cx1*Q(ax1) + cx2*Q(ax2)
   Real cx0, cx1, cx2;
@@ -441,21 +466,21 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
   for (int i = 0; i < S::Q; ++i) {
     const Real* so = Sold + (long long)i * g.Sp;
     const Real* sn = Snew + (long long)i * g.Sp;
-    Real gq = 0;
+    Real gq = 0;   // sigma_y c_x dQ/dx + sigma_x c_y dQ/dy, with 2Q
     if (S::ex(i) != 0) {
       const Real dx = cx0 * (__ldg(so + ax0) + __ldg(sn + ax0)) +
                       cx1 * (__ldg(so + ax1) + __ldg(sn + ax1)) +
                       cx2 * (__ldg(so + ax2) + __ldg(sn + ax2));
-      gq += Real(S::ex(i)) * dx;
+      gq += sy * Real(S::ex(i)) * dx;
     }
     if (S::ey(i) != 0) {
       const Real dy = cy0 * (__ldg(so + ay0) + __ldg(sn + ay0)) +
                       cy1 * (__ldg(so + ay1) + __ldg(sn + ay1)) +
                       cy2 * (__ldg(so + ay2) + __ldg(sn + ay2));
-      gq += Real(S::ey(i)) * dy;
+      gq += sx * Real(S::ey(i)) * dy;
     }
     Real* b = B + (long long)i * g.plane + idx;
-    *b = *b - sig * Real(0.5) * gq;   // Q = (S^(n-1) + S^n) / 2
+    *b = *b - Real(0.5) * gq;   // Q = (S^(n-1) + S^n) / 2
   }
 }
 

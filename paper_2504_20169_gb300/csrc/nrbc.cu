@@ -62,7 +62,8 @@ __device__ inline void char_rate(const BcParams& bc, int variant, double out, co
 // memory (fluid moments Ue frozen at time n). Block = one edge, tangential chunk [t0, t0 + T)
 // plus a 4-node halo on each side where the chunk does not end the band; thread = (layer,
 // position). Each stage shrinks the valid range by one node at a chunk cut, so the chunk's own
-// nodes see exactly the values a full-band evaluation would.
+// nodes see exactly the values a full-band evaluation would. On a periodic y axis the W and E
+// bands wrap around (central tangential differences everywhere, halo taken modulo Ly).
 constexpr int kChunk = 32, kHalo = 4, kText = kChunk + 2 * kHalo;
 
 template <class R>
@@ -82,7 +83,11 @@ __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
   const bool xaxis = e < 2;
   const double out = (e == 0 || e == 2) ? -1.0 : 1.0;
   const int t0 = k * kChunk;
-  const int lo = max(0, t0 - kHalo), hi = min(len, t0 + kChunk + kHalo);
+  // along a periodic y axis the W / E bands are closed loops: the halo wraps around
+  const bool wrap = g.py && e < 2;
+  const int lo = wrap ? t0 - kHalo : max(0, t0 - kHalo);
+  const int hi = wrap ? t0 + kChunk + kHalo : min(len, t0 + kChunk + kHalo);
+  auto wr = [&](int tt) { return wrap ? ((tt % len) + len) % len : tt; };
   // shared state: [4 buffers][4 comps][M][kText] : V0, stage a, stage b, accumulator
   extern __shared__ double sm[];
   const int plane = M * kText;
@@ -93,7 +98,7 @@ __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
   const int j = tid / kText + 1, t = lo + tid % kText;
   const bool live = j <= M && t < hi;
   if (live)
-    for (int q = 0; q < 4; ++q) at(0, q, j, t) = Vg[q * g.nb + off + (j - 1) * len + t];
+    for (int q = 0; q < 4; ++q) at(0, q, j, t) = Vg[q * g.nb + off + (j - 1) * len + wr(t)];
   __syncthreads();
   auto prim = [&](int buf, int jj, int tt) {
     Prim u;
@@ -104,20 +109,22 @@ __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
     u.T = at(buf, 3, jj, tt);
     return u;
   };
-  auto fluid = [&](int layer, int tt) { return load_prim(Ue, g.ne, ueoff + layer * len + tt, xaxis); };
+  auto fluid = [&](int layer, int tt) {
+    return load_prim(Ue, g.ne, ueoff + layer * len + wr(tt), xaxis);
+  };
   const int variant = bc.edge[e];
   double kk[4] = {0, 0, 0, 0};
   for (int s = 1; s <= 4; ++s) {
     const int in_buf = s == 1 ? 0 : (s == 3 ? 2 : 1);  // V0, a, b, a
-    const int slo = lo == 0 ? 0 : lo + s, shi = hi == len ? len : hi - s;
+    const int slo = (!wrap && lo == 0) ? 0 : lo + s, shi = (!wrap && hi == len) ? len : hi - s;
     if (live && t >= slo && t < shi) {
       const Prim U0 = prim(in_buf, j, t);
       const Prim U1 = j >= 2 ? prim(in_buf, j - 1, t) : fluid(0, t);
       const Prim U2 = j >= 3 ? prim(in_buf, j - 2, t) : (j == 2 ? fluid(0, t) : fluid(1, t));
       int ta;
       double ca, cb, cc;
-      if (t == 0) { ta = 0; ca = -1.5; cb = 2.0; cc = -0.5; }
-      else if (t == len - 1) { ta = t - 2; ca = 0.5; cb = -2.0; cc = 1.5; }
+      if (!wrap && t == 0) { ta = 0; ca = -1.5; cb = 2.0; cc = -0.5; }
+      else if (!wrap && t == len - 1) { ta = t - 2; ca = 0.5; cb = -2.0; cc = 1.5; }
       else { ta = t - 1; ca = -0.5; cb = 0.0; cc = 0.5; }
       Prim Va = U0, Vb = U0, Vc = U0;
       if (variant != 0) {
@@ -136,7 +143,7 @@ __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
           at(out_buf, q, j, t) = at(0, q, j, t) + a * kk[q];
           at(3, q, j, t) = (s == 1 ? 0.0 : at(3, q, j, t)) + wgt * kk[q];
         }
-      } else if (t >= t0 && t < t0 + kChunk) {
+      } else if (t >= t0 && t < t0 + kChunk && t < len) {
         const double sixth = 1.0 / 6.0;
         for (int q = 0; q < 4; ++q)
           Vg[q * g.nb + off + (j - 1) * len + t] = at(0, q, j, t) + (at(3, q, j, t) + kk[q]) * sixth;

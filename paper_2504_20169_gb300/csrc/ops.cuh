@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) k_fields(Geom g, Consts<Real> c, const Re
                                                 const double* r2, const double* r3,
                                                 double* partials, int mode) {
   const int nxr = region ? g.Lx : g.nx, nyr = region ? g.Ly : g.ny;
-  const int offx = region ? 0 : g.W, offy = region ? 0 : g.Wy;
+  const int offx = region ? 0 : g.Ww, offy = region ? 0 : g.Ws;
   const int xr = blockIdx.x * blockDim.x + threadIdx.x;
   const int yr = blockIdx.y * blockDim.y + threadIdx.y;
   const bool live = xr < nxr && yr < nyr;
@@ -193,11 +193,11 @@ struct Ops {
     mark(4, bs);
     bool fused = false;
     if constexpr (DEV) {
-      if (g.W > 0 || g.Wy > 0) {
+      if (has_pml(g)) {
         // FP32: single-pass frame (tile + halo in shared memory)
         const FrameTiles ft = make_frame_tiles(g, 256);
         const size_t smem = pml_fused_smem<S>(ft);
-        k_pml_fused<S, STREAM><<<ft.n_tb + ft.n_side, 256, smem, bs>>>(
+        k_pml_fused<S, STREAM><<<frame_tile_count(ft), 256, smem, bs>>>(
             g, c, ft, A, B, static_cast<const float*>(d.Sold), static_cast<float*>(d.Snew),
             d.Uedge, d.bc.bc == 2 ? 1 : 0, d.flag);
         fused = true;
@@ -209,7 +209,7 @@ struct Ops {
           d.bc.bc == 2 ? 1 : 0, d.flag);
     mark(5, bs);
     mark(6, bs);
-    if ((g.W > 0 || g.Wy > 0) && !fused)
+    if (has_pml(g) && !fused)
       k_frame2<S, Real><<<(g.frame_n + 127) / 128, 128, 0, bs>>>(
           g, c, B, static_cast<const Real*>(d.Sold), static_cast<const Real*>(d.Snew));
     mark(7, bs);
@@ -217,8 +217,8 @@ struct Ops {
     k_gamma<S, Real, DEV, STREAM><<<(g.ngamma + 127) / 128, 128, 0, bs>>>(g, c, d.bc, A, B,
                                                                           d.Vtgt);
     mark(9, bs);
-    const int nbx = (g.Lx - g.Wf - (g.Wf / 32) * 32 + 31) / 32;
-    const int ny_in = g.Ly - 2 * g.Wfy;
+    const int nbx = (g.Lx - g.Fe - (g.Fw / 32) * 32 + 31) / 32;
+    const int ny_in = g.Ly - g.Fs - g.Fn;
     constexpr int BY = 4;
     mark(2, d.st);
     if (nbx > 0 && ny_in > 0) {

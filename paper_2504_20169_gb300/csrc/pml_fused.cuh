@@ -1,47 +1,73 @@
 // Single-pass PML frame kernel (FP32 deviation storage): one block per tile of the frame
-// (P + inner ring, distance < Wf from the edge of F) with a 2-node halo.
+// (P + inner ring: the outer Fw / Fe / Fs / Fn layers of F) with a 2-node halo.
 //
 //  A  every owned node and every node of tile + halo that carries Q (distance <= W along a
 //     PML axis) pulls its populations and takes its moments; the latter store
 //     Q_i = S_i^(n-1) + f_hat_i^n / 2 for all i in shared memory (trapezoidal accumulator,
 //     Eq. PMLQ; f_hat = f_eq - f_eq_bar, Eq. decomp-NJ);
 //  C  every owned node pulls again (cache hits), collides with BGK (moments kept from A),
-//     adds on P the PML term of Eq. (PMLCOLL) with grad Q from shared memory
+//     adds on P the PML term of Eq. (pml-general) (Eq. PMLCOLL when sigma_x = sigma_y) with
+//     grad Q from shared memory
 //     (Eq. FD-dx-center; Eq. FD-dx-bw along the outward normal on the outermost layer; the
 //     2-node halo covers both), writes the post-collision populations and
 //     S^n = S^(n-1) + f_hat^n.
 //
-// Tiles: the bottom and top bands (Wf rows, full width) use 32-wide tiles whose height splits
-// Wf evenly; the left and right bands (Wf columns) use tiles whose width splits Wf evenly.
+// Tiles: the bottom and top bands (Fs / Fn rows, full width) use 32-wide tiles whose height
+// splits the band depth evenly; the left and right bands (Fw / Fe columns of the middle rows)
+// use tiles whose width splits the band depth evenly.
 #pragma once
 #include "lbm_device.cuh"
 
 namespace lbm {
 
-struct FrameTiles {
-  int tb_h, tb_rows, tb_cols;   // top / bottom bands: tile 32 x tb_h
-  int s_w, s_cols, s_h, s_rows; // left / right bands: tile s_w x s_h
-  int n_tb, n_side;             // tile counts (both bands of each kind)
-  int ext_max;                  // largest (w + 4) (h + 4)
+struct BandTiles {
+  int tw, th;        // tile size
+  int cols, rows;    // tiles across / along the band
+  int n;             // cols * rows
 };
+
+struct FrameTiles {
+  BandTiles b[4];    // bottom, top, left, right
+  int ext_max;       // largest (tw + 4) (th + 4)
+};
+
+inline BandTiles row_band(int depth, int Lx) {
+  BandTiles t{};
+  t.tw = 32;
+  t.rows = (depth + 7) / 8;
+  t.th = t.rows > 0 ? (depth + t.rows - 1) / t.rows : 1;
+  t.cols = (Lx + 31) / 32;
+  t.n = t.rows * t.cols;
+  return t;
+}
+
+inline BandTiles column_band(int depth, int height, int threads) {
+  BandTiles t{};
+  t.cols = (depth + 31) / 32;
+  t.tw = (depth + t.cols - 1) / t.cols;
+  t.th = threads / t.tw;
+  if (t.th > 32) t.th = 32;
+  t.rows = (height + t.th - 1) / t.th;
+  t.n = t.rows * t.cols;
+  return t;
+}
 
 inline FrameTiles make_frame_tiles(const Geom& g, int threads) {
   FrameTiles t{};
-  const int Wf = g.Wf, Wfy = g.Wfy;
-  t.tb_rows = (Wfy + 7) / 8;
-  t.tb_h = t.tb_rows > 0 ? (Wfy + t.tb_rows - 1) / t.tb_rows : 1;
-  t.tb_cols = (g.Lx + 31) / 32;
-  t.s_cols = (Wf + 31) / 32;
-  t.s_w = (Wf + t.s_cols - 1) / t.s_cols;
-  t.s_h = threads / t.s_w;
-  if (t.s_h > 32) t.s_h = 32;
-  t.s_rows = (g.Ly - 2 * Wfy + t.s_h - 1) / t.s_h;
-  t.n_tb = 2 * t.tb_rows * t.tb_cols;
-  t.n_side = 2 * t.s_cols * t.s_rows;
-  const int e1 = (32 + 4) * (t.tb_h + 4), e2 = (t.s_w + 4) * (t.s_h + 4);
-  t.ext_max = e1 > e2 ? e1 : e2;
+  const int mid = g.Ly - g.Fs - g.Fn;
+  t.b[0] = row_band(g.Fs, g.Lx);
+  t.b[1] = row_band(g.Fn, g.Lx);
+  t.b[2] = column_band(g.Fw, mid, threads);
+  t.b[3] = column_band(g.Fe, mid, threads);
+  t.ext_max = 0;
+  for (int k = 0; k < 4; ++k) {
+    const int e = (t.b[k].tw + 4) * (t.b[k].th + 4);
+    if (t.b[k].n > 0 && e > t.ext_max) t.ext_max = e;
+  }
   return t;
 }
+
+inline int frame_tile_count(const FrameTiles& t) { return t.b[0].n + t.b[1].n + t.b[2].n + t.b[3].n; }
 
 // shared memory of k_pml_fused: Q on the extended tile and the moments of the owned nodes
 template <class S>
@@ -61,26 +87,16 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   int x0, y0, tw, th, band;  // band 0 bottom, 1 top, 2 left, 3 right
   {
     int k = blockIdx.x;
-    if (k < ft.n_tb) {
-      const int per = ft.tb_rows * ft.tb_cols;
-      band = k < per ? 0 : 1;
-      k -= band * per;
-      const int r = k / ft.tb_cols, cc = k - r * ft.tb_cols;
-      tw = 32;
-      th = ft.tb_h;
-      x0 = cc * 32;
-      y0 = band == 0 ? r * th : g.Ly - g.Wfy + r * th;
-    } else {
-      k -= ft.n_tb;
-      const int per = ft.s_cols * ft.s_rows;
-      band = k < per ? 2 : 3;
-      k -= (band - 2) * per;
-      const int r = k / ft.s_cols, cc = k - r * ft.s_cols;
-      tw = ft.s_w;
-      th = ft.s_h;
-      x0 = band == 2 ? cc * tw : g.Lx - g.Wf + cc * tw;
-      y0 = g.Wfy + r * th;
-    }
+    band = 0;
+    while (band < 3 && k >= ft.b[band].n) k -= ft.b[band++].n;
+    const BandTiles& bt = ft.b[band];
+    const int r = k / bt.cols, cc = k - r * bt.cols;
+    tw = bt.tw;
+    th = bt.th;
+    if (band == 0) { x0 = cc * tw; y0 = r * th; }
+    else if (band == 1) { x0 = cc * tw; y0 = g.Ly - g.Fn + r * th; }
+    else if (band == 2) { x0 = cc * tw; y0 = g.Fs + r * th; }
+    else { x0 = g.Lx - g.Fe + cc * tw; y0 = g.Fs + r * th; }
   }
   const int ew = tw + 4, eh = th + 4, next = ew * eh;
   const int nown = tw * th;
@@ -130,10 +146,10 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   const int x = x0 + tx, y = y0 + ty;
   if (x >= g.Lx || y >= g.Ly) return;
   bool owned;
-  if (band == 0) owned = y < g.Wfy;
-  else if (band == 1) owned = y >= g.Ly - g.Wfy;
-  else if (band == 2) owned = x < g.Wf && y < g.Ly - g.Wfy;
-  else owned = y < g.Ly - g.Wfy;
+  if (band == 0) owned = y < g.Fs;
+  else if (band == 1) owned = y >= g.Ly - g.Fn;
+  else if (band == 2) owned = x < g.Fw && y < g.Ly - g.Fn;
+  else owned = y < g.Ly - g.Fn;
   if (!owned) return;
   const int d = dist_out(g, x, y);
   const long long idx = gindex(g, x, y);
@@ -154,7 +170,9 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   const int e0 = (ty + 2) * ew + (tx + 2);
   const PmlNode<float> pn = pml_node<float>(g, x, y);
   const bool in_p = pn.in_p;
-  const float sig = in_p ? sigma_of(c, pn.frac) : 0.f;
+  float sx = 0.f, sy = 0.f;
+  if (in_p) pml_sigmas(c, pn, sx, sy);
+  const float ssum = sx + sy, sprod = sx * sy;
   // gradient stencils on the shared-memory tile (offsets in extended-tile units)
   float cx0 = 0.5f, cx1 = -0.5f, cx2 = 0.f, cy0 = 0.5f, cy1 = -0.5f, cy2 = 0.f;
   int ox0 = 1, ox1 = -1, ox2 = 0, oy0 = ew, oy1 = -ew, oy2 = 0;
@@ -173,10 +191,10 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
     Snew[(long long)i * g.Sp + fi] = __ldg(Sold + (long long)i * g.Sp + fi) + fhat;  // S^n
     float out = p[i] + c.omega * (eq - p[i]);
     if (in_p) {
-      float gq = 0.f;
-      if (S::ex(i) != 0) gq += float(S::ex(i)) * (cx0 * q[ox0] + cx1 * q[ox1] + cx2 * q[ox2]);
-      if (S::ey(i) != 0) gq += float(S::ey(i)) * (cy0 * q[oy0] + cy1 * q[oy1] + cy2 * q[oy2]);
-      out = out - sig * (gq + 2.f * fhat + sig * qn);
+      float gq = 0.f;   // sigma_y c_x dQ/dx + sigma_x c_y dQ/dy
+      if (S::ex(i) != 0) gq += sy * float(S::ex(i)) * (cx0 * q[ox0] + cx1 * q[ox1] + cx2 * q[ox2]);
+      if (S::ey(i) != 0) gq += sx * float(S::ey(i)) * (cy0 * q[oy0] + cy1 * q[oy1] + cy2 * q[oy2]);
+      out = out - (gq + ssum * fhat + sprod * qn);
     }
     B[(long long)i * g.plane + idx] = out;
   }

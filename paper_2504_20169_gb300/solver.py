@@ -40,25 +40,28 @@ def _host(a):
 class Solver:
     def __init__(self, nx, ny, W, tau, sigma_max=0.0, sigma_power=2, bc="zg", q=37,
                  nrbc_edges=(0, 0, 0, 0), beta=0.0, mean=(1.0, 0.0, 0.0, 1.0), relax_sign=-1.0,
-                 precision="fp64", stream=None, pml_width_y=None, periodic_y=False):
-        """W: PML layers on the W/E edges (and S/N unless pml_width_y is given); periodic_y:
-        the y axis wraps (no S/N boundary, no PML there)."""
+                 precision="fp64", stream=None, pml_widths=None, periodic_y=False,
+                 sigma_split=False):
+        """W: PML layers on every edge, unless pml_widths = (W_w, W_e, W_s, W_n) is given;
+        periodic_y: the y axis wraps (no S/N boundary, no PML there); sigma_split: the
+        sigma_x != sigma_y form of Eq. (pml-general)."""
         import torch
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.nx, self.ny, self.W, self.q = nx, ny, W, q
-        self.Wy = 0 if periodic_y else (W if pml_width_y is None else pml_width_y)
-        self.Lx, self.Ly = nx + 2 * W, ny + 2 * self.Wy
         self.precision = precision
         grid = L.lbm_grid(nx, ny)
-        sig = L.lbm_sigma_profile(sigma_max, sigma_power)
+        sig = L.lbm_sigma_profile(sigma_max, sigma_power, 1 if sigma_split else 0)
         bp = L.lbm_bc_params()
         for k in range(4):
             bp.edge[k] = int(nrbc_edges[k])
         bp.beta = beta
         bp.relax_sign = relax_sign
         bp.rho0, bp.u0x, bp.u0y, bp.T0 = mean
-        bp.pml_width_y = -1 if pml_width_y is None else int(pml_width_y)
+        if pml_widths is not None:
+            bp.use_pml_widths = 1
+            for k in range(4):
+                bp.pml_widths[k] = int(pml_widths[k])
         bp.periodic_y = 1 if periodic_y else 0
         out = C.c_void_p()
         with torch.cuda.device(self.stream.device):
@@ -66,9 +69,11 @@ class Solver:
                                       C.byref(bp), _PREC[precision],
                                       C.c_void_p(self.stream.cuda_stream), C.byref(out)))
         self.ctx = out
-        g = (C.c_int64 * 8)()
+        g = (C.c_int64 * 12)()
         _check(L.lib().lbm_geometry(self.ctx, g), self.ctx)
         self.M = int(g[3])
+        self.Lx, self.Ly = int(g[4]), int(g[5])
+        self.widths = tuple(int(v) for v in g[8:12])
 
     # ---------------------------------------------------------------- lifecycle
     def close(self):
@@ -175,6 +180,6 @@ class Solver:
 
     @property
     def steps(self):
-        g = (C.c_int64 * 8)()
+        g = (C.c_int64 * 12)()
         _check(L.lib().lbm_geometry(self.ctx, g), self.ctx)
         return int(g[7])

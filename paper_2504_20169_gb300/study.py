@@ -1,4 +1,12 @@
-"""The thermal-vortex boundary study of Sec. 5.2, run on the GPU through the public API.
+"""The boundary studies of Sec. 5, run on the GPU through the public API.
+
+Density step (Sec. 5.1, `run_density_step`): 200 x 20 bulk, periodic y axis, Mach 0.05 mean
+flow along x, the tanh density step (workloads.density_step), D2Q9 / D2Q17 / D2Q37. Cases per
+stencil: ZG and PNR-LODI without PML, and with PML W = 10 / 20 / 40 on the two x edges with
+the sigma_max of Table 1 (quadratic ramp). Errors e_rho, e_ux against a periodic reference on
+an x-padded grid, sampled every `sample` steps; C_Z and C_t relative to ZG without PML, as below.
+
+Thermal vortex (Sec. 5.2, `run`):
 
 D2Q17 (third-order equilibrium), 300 x 300 bulk, every edge open, Mach 0.1 mean flow, the
 vortex of Sec. 5.2 (workloads.paper_vortex). Cases, as in Figs. 8-9:
@@ -16,7 +24,8 @@ characteristic targets and the boundary band; t_ZG the band time of ZG without P
 kernel class is timed alone with CUDA events (lbm_profile_*).
 The paper leaves tau and the vortex's b, r*, K open; tau = 0.8, b = 0.2, r* = 0.5, K = 180.
 
-Run: python -m paper_2504_20169_gb300.study   (prints one JSON line per case and a table)
+Run: python -m paper_2504_20169_gb300.study [--case vortex|step|all]   (one JSON line per case
+and a table)
 """
 from __future__ import annotations
 
@@ -90,24 +99,117 @@ def run(L=300, steps=1500, sample=50, tau=0.8, Ma=0.1, q=17, precision="fp64", p
     return meta, results
 
 
+# Table 1: sigma_max of the density-step runs per stencil, boundary condition and width
+STEP_SIGMA = {
+    9: {"ZG": {10: 0.17, 20: 0.10, 40: 0.07}, "LODI": {10: 0.001, 20: 0.04, 40: 0.04}},
+    17: {"ZG": {10: 0.33, 20: 0.14, 40: 0.09}, "LODI": {10: 0.001, 20: 0.08, 40: 0.04}},
+    37: {"ZG": {10: 0.35, 20: 0.175, 40: 0.10}, "LODI": {10: 0.001, 20: 0.10, 40: 0.06}},
+}
+
+
+def step_cases(q):
+    out = [("ZG", "zg", 0, 0.0), ("LODI", "nrbc", 0, 0.0)]
+    for W in (10, 20, 40):
+        out += [("ZG", "zg", W, STEP_SIGMA[q]["ZG"][W]), ("LODI", "nrbc", W, STEP_SIGMA[q]["LODI"][W])]
+    return out
+
+
+def run_density_step(q=37, Lx=200, Ly=20, steps=2000, sample=20, tau=0.8, Ma=0.05,
+                     precision="fp64", prof_steps=100):
+    import torch
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import workloads as wl
+    from . import Solver, lattice_info
+    _, _, r = lattice_info(q)
+    speed = (math.sqrt(2.0) + Ma) / r
+    pad = int(speed * steps * 1.05) + 8
+    refs = []
+    # reference: periodic in x and y on an x-padded grid; the formula continues into the pad
+    with Solver(Lx + 2 * pad, Ly, 0, tau, bc="periodic", q=q, precision=precision) as ref:
+        fr = wl.density_step(Lx, Ly, Ma=Ma, W=(pad, pad, 0, 0))
+        ref.init(*fr)
+        for k in range(steps // sample):
+            ref.step(sample)
+            f = ref.moments(region="F", device=True)
+            refs.append([t[:, pad:pad + Lx].contiguous() for t in f])
+    results = []
+    mean = (1.0, Ma, 0.0, 1.0)
+    for label, bc, W, sig in step_cases(q):
+        s = Solver(Lx, Ly, W, tau, sig, 2, bc, q, (0, 0, 0, 0), 0.0, mean,
+                   precision=precision, periodic_y=True)
+        fields = wl.density_step(Lx, Ly, Ma=Ma, W=W, Wy=0)
+        s.init(*fields)
+        e = {"rho": [], "ux": []}
+        status = "ok"
+        try:
+            for k in range(steps // sample):
+                s.step(sample)
+                sums = s.error_sums(refs[k])
+                e["rho"].append(math.sqrt(sums[2]))
+                e["ux"].append(math.sqrt(sums[5]))
+        except Exception as ex:
+            status = str(ex).split(":")[0] + f" after <= {(len(e['rho']) + 1) * sample} steps"
+        s.init(*fields)
+        s.profile_enable(prof_steps)
+        s.step(prof_steps)
+        ms, n = s.profile_read()
+        s.close()
+        t_bc = (ms["frame1"] + ms["frame2"] if W > 0 else 0.0) + ms["targets"] + ms["band"]
+        results.append({"q": q, "bc": label, "W": W, "sigma_max": sig, "status": status,
+                        "ebar": {k: (sum(v) / len(v) if v and status == "ok" else None)
+                                 for k, v in e.items()},
+                        "emax": {k: (max(v) if v and status == "ok" else None)
+                                 for k, v in e.items()},
+                        "t_bc_us": 1e3 * t_bc / n})
+    base = results[0]
+    for r_ in results:
+        r_["C_Z"] = {k: (r_["ebar"][k] / base["ebar"][k]
+                         if r_["ebar"][k] and base["ebar"][k] else None) for k in r_["ebar"]}
+        r_["C_t"] = r_["t_bc_us"] / base["t_bc_us"]
+    meta = {"case": "density_step", "Lx": Lx, "Ly": Ly, "steps": steps, "sample": sample,
+            "tau": tau, "Ma": Ma, "q": q, "precision": precision,
+            "reference_grid": [Lx + 2 * pad, Ly]}
+    return meta, results
+
+
+def _fmt(v):
+    return "n/a" if v is None else f"{v:.3g}"
+
+
 def main():
     import argparse
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="all", choices=("vortex", "step", "all"))
     ap.add_argument("--tau", type=float, default=0.8)
-    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--steps", type=int, default=None)
     a = ap.parse_args()
-    meta, results = run(steps=a.steps, tau=a.tau)
-    print(json.dumps(meta))
-    for r in results:
-        print(json.dumps(r))
-    print("| BC | W | sigma_max | e_bar rho | e_bar u_x | e_bar T | C_rho | C_ux | C_T | C_t |")
-    print("|---|---|---|---|---|---|---|---|---|---|")
-    for r in results:
-        eb, cz = r["ebar"], r["C_Z"]
-        f = lambda v: "n/a" if v is None else f"{v:.3g}"
-        print(f"| {r['bc']} | {r['W']} | {r['sigma_max']} | {f(eb['rho'])} | {f(eb['ux'])} | "
-              f"{f(eb['T'])} | {f(cz['rho'])} | {f(cz['ux'])} | {f(cz['T'])} | {r['C_t']:.1f} |"
-              + ("" if r["status"] == "ok" else f" {r['status']}"))
+    if a.case in ("step", "all"):
+        print("| q | BC | W | sigma_max | e_bar rho | e_bar u_x | max e rho | C_rho | C_ux | C_t |")
+        print("|---|---|---|---|---|---|---|---|---|---|")
+        for q in (9, 17, 37):
+            meta, results = run_density_step(q=q, steps=a.steps or 2000, tau=a.tau)
+            print(json.dumps(meta))
+            for r in results:
+                print(json.dumps(r))
+            for r in results:
+                eb, cz = r["ebar"], r["C_Z"]
+                print(f"| {q} | {r['bc']} | {r['W']} | {r['sigma_max']} | {_fmt(eb['rho'])} | "
+                      f"{_fmt(eb['ux'])} | {_fmt(r['emax']['rho'])} | {_fmt(cz['rho'])} | "
+                      f"{_fmt(cz['ux'])} | {r['C_t']:.1f} |"
+                      + ("" if r["status"] == "ok" else f" {r['status']}"))
+    if a.case in ("vortex", "all"):
+        meta, results = run(steps=a.steps or 1500, tau=a.tau)
+        print(json.dumps(meta))
+        for r in results:
+            print(json.dumps(r))
+        print("| BC | W | sigma_max | e_bar rho | e_bar u_x | e_bar T | C_rho | C_ux | C_T | C_t |")
+        print("|---|---|---|---|---|---|---|---|---|---|")
+        for r in results:
+            eb, cz = r["ebar"], r["C_Z"]
+            print(f"| {r['bc']} | {r['W']} | {r['sigma_max']} | {_fmt(eb['rho'])} | "
+                  f"{_fmt(eb['ux'])} | {_fmt(eb['T'])} | {_fmt(cz['rho'])} | {_fmt(cz['ux'])} | "
+                  f"{_fmt(cz['T'])} | {r['C_t']:.1f} |"
+                  + ("" if r["status"] == "ok" else f" {r['status']}"))
 
 
 if __name__ == "__main__":

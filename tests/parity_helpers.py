@@ -8,16 +8,17 @@ from oracle import OracleLBM
 def case_kwargs(**kw):
     base = dict(nx=32, ny=32, W=4, tau=0.8, sigma_max=0.1, sigma_power=3, bc="zg", q=37,
                 nrbc_edges=(0, 0, 0, 0), beta=0.0, mean=(1.0, 0.0, 0.0, 1.0), relax_sign=-1.0,
-                Wy=None, periodic_y=False)
+                widths=None, periodic_y=False, split=False)
     base.update(kw)
     return base
 
 
 def run_oracle(kw, fields, steps):
-    o = OracleLBM(kw["nx"], kw["ny"], kw["W"], kw["tau"], kw["sigma_max"], kw["sigma_power"],
+    W = kw["W"] if kw["widths"] is None else tuple(kw["widths"])
+    o = OracleLBM(kw["nx"], kw["ny"], W, kw["tau"], kw["sigma_max"], kw["sigma_power"],
                   kw["bc"], q=kw["q"], nrbc_edges=kw["nrbc_edges"], beta=kw["beta"],
-                  mean=kw["mean"], relax_sign=kw["relax_sign"], Wy=kw["Wy"],
-                  periodic_y=kw["periodic_y"])
+                  mean=kw["mean"], relax_sign=kw["relax_sign"],
+                  periodic_y=kw["periodic_y"], sigma_split=kw["split"])
     o.init(*fields)
     o.step(steps)
     return o.fields(), o
@@ -27,8 +28,8 @@ def make_solver(kw, precision="fp64"):
     from paper_2504_20169_gb300 import Solver
     return Solver(kw["nx"], kw["ny"], kw["W"], kw["tau"], kw["sigma_max"], kw["sigma_power"],
                   kw["bc"], kw["q"], kw["nrbc_edges"], kw["beta"], kw["mean"],
-                  kw["relax_sign"], precision, pml_width_y=kw["Wy"],
-                  periodic_y=kw["periodic_y"])
+                  kw["relax_sign"], precision, pml_widths=kw["widths"],
+                  periodic_y=kw["periodic_y"], sigma_split=kw["split"])
 
 
 def run_gpu(kw, fields, steps, precision="fp64"):

@@ -122,14 +122,17 @@ def test_parity_nrbc_band_lengths(nx, ny, W, steps, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
-@pytest.mark.parametrize("bc,W", [("zg", 0), ("zg", 8), ("nrbc", 0), ("nrbc", 8)])
-def test_parity_periodic_y_axis(bc, W, precision):
-    """Sec. 5.1 setting: periodic y axis, PML (or none) and ZG / PNR-LODI on the x edges. The
-    density step of Sec. 5.1 plus a y-dependent smooth perturbation, so that the wrapped rows,
-    the wrapped halo of the frame kernel and the y-central PML gradient all matter."""
+@pytest.mark.parametrize("bc,W,edges", [("zg", 0, None), ("zg", 8, None), ("nrbc", 0, (0, 0)),
+                                        ("nrbc", 8, (0, 0)), ("nrbc", 8, (1, 1))])
+def test_parity_periodic_y_axis(bc, W, edges, precision):
+    """Sec. 5.1 setting: periodic y axis, PML (or none) and ZG / PNR-LODI / CBC relax on the x
+    edges. The density step of Sec. 5.1 plus a y-dependent smooth perturbation, so that the
+    wrapped rows, the wrapped halo of the frame kernel, the y-central PML gradient and the
+    wrapped tangential derivative of the characteristic targets all matter."""
     nx, ny = 60, 20
+    ed = (0, 0, 0, 0) if edges is None else (edges[0], edges[1], 0, 0)
     kw = case_kwargs(nx=nx, ny=ny, W=W, tau=0.7, sigma_max=0.05, sigma_power=2, bc=bc,
-                     mean=(1.0, 0.05, 0.0, 1.0), Wy=0, periodic_y=True)
+                     nrbc_edges=ed, beta=0.2, mean=(1.0, 0.05, 0.0, 1.0), periodic_y=True)
     rho, ux, uy, T = wl.density_step(nx, ny, Ma=0.05, W=W, Wy=0)
     pr, pux, puy, pT = wl.random_smooth_state(nx, ny, W, seed=21, du=0.02, Wy=0)
     fields = (rho + pr - 1.0, ux + pux, uy + puy, T + pT - 1.0)
@@ -137,17 +140,33 @@ def test_parity_periodic_y_axis(bc, W, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
-@pytest.mark.parametrize("nx,ny,W,Wy,bc", [(40, 30, 6, 3, "zg"), (36, 44, 0, 5, "nrbc"),
-                                           (50, 26, 7, 0, "zg"), (30, 34, 2, 9, "nrbc")])
-def test_parity_per_axis_pml_widths(nx, ny, W, Wy, bc, precision):
-    """Different PML widths on the x and y edges (one of them possibly 0): frame depths per
-    axis, the layer fraction max(i_x / W, i_y / Wy) in the corners, Q support per axis.
-    PNR-LODI edges: with CBC relax next to unequal widths the oracle itself diverges within
-    40 steps on these grids."""
-    kw = case_kwargs(nx=nx, ny=ny, W=W, tau=0.75, sigma_max=0.15, sigma_power=2, bc=bc,
-                     nrbc_edges=(0, 0, 0, 0), mean=(1.0, 0.05, 0.02, 1.0), Wy=Wy)
-    fields = wl.random_smooth_state(nx, ny, W, seed=nx * ny + W, du=0.04,
-                                    mean_u=(0.05, 0.02), Wy=Wy)
+@pytest.mark.parametrize("nx,ny,widths,bc", [
+    (40, 30, (6, 6, 3, 3), "zg"), (36, 44, (0, 0, 5, 5), "nrbc"), (50, 26, (7, 7, 0, 0), "zg"),
+    (30, 34, (2, 2, 9, 9), "nrbc"), (48, 36, (3, 12, 2, 4), "zg"), (40, 40, (0, 16, 0, 0), "nrbc"),
+    (44, 30, (4, 10, 4, 4), "nrbc"), (33, 41, (35, 2, 0, 6), "zg")])
+def test_parity_per_edge_pml_widths(nx, ny, widths, bc, precision):
+    """Per-edge PML widths (thin layers away from the outlet, some edges without PML): frame
+    depths per edge, layer fractions per edge, Q support per edge, tiles of four different
+    band depths. PNR-LODI edges: with CBC relax next to unequal widths the oracle itself
+    diverges within 40 steps on these grids."""
+    kw = case_kwargs(nx=nx, ny=ny, W=0, tau=0.75, sigma_max=0.15, sigma_power=2, bc=bc,
+                     mean=(1.0, 0.05, 0.02, 1.0), widths=widths)
+    fields = wl.random_smooth_state(nx, ny, widths, seed=nx * ny + sum(widths), du=0.04,
+                                    mean_u=(0.05, 0.02))
+    check(kw, fields, 30, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+@pytest.mark.parametrize("widths,bc", [((6, 6, 6, 6), "zg"), ((4, 10, 3, 5), "nrbc"),
+                                       ((8, 8, 0, 0), "zg")])
+def test_parity_split_sigma(widths, bc, precision):
+    """The general sigma_x != sigma_y form of Eq. (pml-general): sigma_x from the x layers,
+    sigma_y from the y layers, each damping the other axis's gradient."""
+    nx, ny = 40, 36
+    kw = case_kwargs(nx=nx, ny=ny, W=0, tau=0.75, sigma_max=0.2, sigma_power=2, bc=bc,
+                     mean=(1.0, 0.04, -0.02, 1.0), widths=widths, split=True)
+    fields = wl.random_smooth_state(nx, ny, widths, seed=77 + sum(widths), du=0.04,
+                                    mean_u=(0.04, -0.02))
     check(kw, fields, 30, precision)
 
 

@@ -267,3 +267,83 @@ def test_per_axis_pml_widths_transpose():
     assert sa[Wy + 5, 0] == pytest.approx(0.1) and sa[0, W + 5] == pytest.approx(0.1)
     assert sa[Wy + 5, 1] == pytest.approx(0.1 * (5 / 6) ** 2)
     assert sa[1, W + 5] == pytest.approx(0.1 * (2 / 3) ** 2)
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_pml_first_step_closed_form(split):
+    """Uniform density excess delta at rest, sigma = sigma_max on all of P (p = 0), Q^0 = 0:
+    the first step adds -(sigma_x + sigma_y) f_hat (Eq. pml-general), and a node whose pull
+    sources all lie in one zone reads rho = 1 + delta (1 - sigma_x - sigma_y), T = 1, u = 0.
+    Equal sigmas (Eq. PMLCOLL): 1 - 2 sigma on all of P. Split: 1 - sigma in a slab, 1 - 2 sigma
+    in a corner. Bulk: 1 + delta."""
+    nx, W, s, d = 16, 10, 0.05, 1e-3
+    o = OracleLBM(nx, nx, W, 0.7, s, 0, "zg", sigma_split=split)
+    L = nx + 2 * W
+    o.init(*wl.uniform(nx, nx, W, rho=1.0 + d))
+    o.step(1)
+    rho, ux, uy, T = o.fields("F")
+    slab = rho[L // 2, 5]
+    corner = rho[5, 5]
+    bulk = rho[L // 2, L // 2]
+    assert bulk == pytest.approx(1.0 + d, abs=1e-14)
+    assert slab == pytest.approx(1.0 + d * (1.0 - (1.0 if split else 2.0) * s), abs=1e-14)
+    assert corner == pytest.approx(1.0 + d * (1.0 - 2.0 * s), abs=1e-14)
+    for z in (slab, corner):
+        assert abs(z - (1.0 + d)) > 0.5 * s * d          # the term acted
+    for (y, x) in ((L // 2, 5), (5, 5), (L // 2, L // 2)):
+        assert abs(T[y, x] - 1.0) < 1e-13 and abs(ux[y, x]) < 1e-13 and abs(uy[y, x]) < 1e-13
+
+
+def test_split_x_slab_ignores_the_x_gradient(monkeypatch):
+    """In the split form the x derivative of Q is weighted by sigma_y, which is zero in a PML
+    slab on the x edges: on a y-periodic grid with PML only on the x edges and a y-invariant
+    state, scaling the x derivative changes nothing (and changes the sigma_x = sigma_y run)."""
+    nx, ny, W = 40, 8, 8
+
+    def run(split):
+        o = OracleLBM(nx, ny, W, 0.7, 0.1, 2, "zg", periodic_y=True, sigma_split=split)
+        o.init(*wl.density_step(nx, ny, Ma=0.05, W=W, Wy=0))
+        o.step(12)
+        return o.fields("F")[0]
+
+    base = {sp: run(sp) for sp in (False, True)}
+    orig = pml.gradient
+
+    def scaled(Q, periodic_y=False):
+        gx, gy = orig(Q, periodic_y)
+        return 3.0 * gx, gy
+
+    monkeypatch.setattr(pml, "gradient", scaled)
+    assert np.array_equal(run(True), base[True])
+    assert np.abs(run(False) - base[False]).max() > 1e-9
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_per_edge_widths_mirror(split):
+    """Widths (W_w, W_e) = (3, 7) and the x-mirrored problem with (7, 3): mirrored results
+    (catches a width or a layer fraction taken from the wrong edge)."""
+    nx, ny = 26, 20
+    a = OracleLBM(nx, ny, (3, 7, 4, 2), 0.7, 0.1, 2, "nrbc", sigma_split=split)
+    b = OracleLBM(nx, ny, (7, 3, 4, 2), 0.7, 0.1, 2, "nrbc", sigma_split=split)
+    c = (9.0, 8.0)
+    a.init(*wl.pressure_pulse(nx, ny, (3, 7, 4, 2), amp=1e-3, halfwidth=3.0, center=c))
+    b.init(*wl.pressure_pulse(nx, ny, (7, 3, 4, 2), amp=1e-3, halfwidth=3.0,
+                              center=(nx - 1 - c[0], c[1])))
+    a.step(40)
+    b.step(40)
+    ra, rb = a.fields("F")[0] - 1.0, b.fields("F")[0] - 1.0
+    assert ra.shape == (ny + 6, nx + 10)
+    assert np.abs(ra[:, :3]).max() > 1e-8 and np.abs(ra[:, -7:]).max() > 1e-8
+    assert np.max(np.abs(ra - rb[:, ::-1])) < 1e-13
+
+
+def test_density_step_profile():
+    """Sec. 5.1 initial density: rho0 at both ends, plateau rho1 around the centre, continuous
+    at Lx/2, half-way values at Lx/4 and 3Lx/4 (node counting from 1)."""
+    rho, ux, uy, T = wl.density_step(200, 20, Ma=0.05)
+    r = rho[0]
+    assert r[0] == pytest.approx(1.0, abs=1e-12) and r[-1] == pytest.approx(1.0, abs=1e-12)
+    assert r[99] == pytest.approx(1.05, abs=1e-9) and r[100] == pytest.approx(1.05, abs=1e-9)
+    assert r[49] == pytest.approx(1.025) and r[149] == pytest.approx(1.025)
+    assert np.abs(np.diff(r)).max() < 0.05 * 0.5 / 2 + 1e-12     # no jump anywhere
+    assert np.all(ux == 0.05) and np.all(uy == 0.0) and np.all(T == 1.0)

@@ -28,17 +28,26 @@ import numpy as np
 GAMMA = 2.0  # (D + 2) / D for D = 2, monatomic ideal gas
 
 
-def f_shape(nx: int, ny: int, W: int, Wy: int | None = None) -> tuple[int, int]:
-    """(Ly, Lx) of the fluid region F (W PML layers on the x edges, Wy, default W, on y)."""
+def _edges(W, Wy=None):
+    """(W_w, W_e, W_s, W_n) from W (every edge, or W/E with Wy on S/N) or a 4-tuple."""
+    if np.ndim(W) == 1:
+        return tuple(int(v) for v in W)
     Wy = W if Wy is None else Wy
-    return (ny + 2 * Wy, nx + 2 * W)
+    return (int(W), int(W), int(Wy), int(Wy))
+
+
+def f_shape(nx: int, ny: int, W, Wy=None) -> tuple[int, int]:
+    """(Ly, Lx) of the fluid region F (W PML layers per edge, Wy on the y edges if given, or
+    per-edge widths (W_w, W_e, W_s, W_n))."""
+    ww, we, ws, wn = _edges(W, Wy)
+    return (ny + ws + wn, nx + ww + we)
 
 
 def _bulk_coords(nx, ny, W, Wy=None):
-    Wy = W if Wy is None else Wy
+    ww, we, ws, wn = _edges(W, Wy)
     Ly, Lx = f_shape(nx, ny, W, Wy)
-    y, x = np.meshgrid(np.arange(Ly, dtype=np.float64) - Wy,
-                       np.arange(Lx, dtype=np.float64) - W, indexing="ij")
+    y, x = np.meshgrid(np.arange(Ly, dtype=np.float64) - ws,
+                       np.arange(Lx, dtype=np.float64) - ww, indexing="ij")
     return x, y
 
 
@@ -88,14 +97,16 @@ def isentropic_vortex(nx, ny, W, R=20.0, Mv=0.05, mean_u=(0.3, 0.0), T0=1.0, rho
 
 def density_step(Lx, Ly, Ma=0.05, rho0=1.0, rho1=1.05, s=0.5, W=0, Wy=None):
     """Sec. 5.1 density step on an Lx x Ly bulk (periodic in y in the paper), padded by W
-    nodes on the x edges and Wy (default W) on the y edges; flat rho0 outside the profile."""
-    Wy = W if Wy is None else Wy
-    y, x = np.meshgrid(np.arange(Ly + 2 * Wy, dtype=np.float64) - Wy,
-                       np.arange(Lx + 2 * W, dtype=np.float64) - W, indexing="ij")
+    nodes on the x edges and Wy (default W) on the y edges (or per-edge widths); the profile
+    formula continues into the padding. Background rho0 with a plateau rho1 on
+    [Lx/4, 3Lx/4]. Reading: the printed right branch, rho1 - (rho1 - rho0)/2 (tanh(.) - 1),
+    jumps to 2 rho1 - rho0 at Lx/2 and ends at rho1; with (tanh(.) + 1) it is continuous and
+    returns to rho0, the state of the PML's mean equilibrium."""
+    x, y = _bulk_coords(Lx, Ly, W, Wy)
     xs = x + 1.0  # the paper counts nodes from 1
     half = (rho1 - rho0) / 2.0
     left = rho1 + half * (np.tanh(s * (xs - 0.25 * Lx)) - 1.0)
-    right = rho1 - half * (np.tanh(s * (xs - 0.75 * Lx)) - 1.0)
+    right = rho1 - half * (np.tanh(s * (xs - 0.75 * Lx)) + 1.0)
     rho = np.where(xs <= Lx / 2.0, left, right)
     return rho, np.full_like(rho, Ma), np.zeros_like(rho), np.ones_like(rho)
 
