@@ -10,7 +10,7 @@
 // f^(n+1)(x) = f*^n(x - e_i) (Eq. lbe), collides, and writes f*^(n+1).
 //
 // Work split of one step (all kernels read buffer A and write disjoint parts of buffer B):
-//   k_nrbc_stage x4   characteristic targets U_tgt^(n+1) on the edge bands (Sec. 4)
+//   k_nrbc_rk4        characteristic targets U_tgt^(n+1) on the edge bands, four RK4 stages (Sec. 4)
 //   k_bulk            nodes of F inside the frame depths (Fw, Fe, Fs, Fn): BGK only
 //   k_frame1          the frame (the outer Fw / Fe / Fs / Fn layers of F): BGK, PML
 //                     accumulator, local PML terms,
