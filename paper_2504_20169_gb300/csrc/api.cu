@@ -177,7 +177,7 @@ struct lbm_ctx {
   void* f[2] = {nullptr, nullptr};
   void* S[2] = {nullptr, nullptr};
   double* V = nullptr;        // 4 arrays of [4][nb]: targets, stage a, stage b, accumulator
-  double* Uedge = nullptr;
+  double* Uedge = nullptr;    // two buffers of [4][ne] (ping-pong with the populations)
   double* staging = nullptr;  // [4][Lx*Ly]
   double* partials = nullptr;
   int max_blocks = 0;
@@ -189,8 +189,8 @@ struct lbm_ctx {
   int cur = 0, scur = 0;
   bool initialized = false, prev_valid = false, prev_prestream = false;
   long long steps = 0;
-  cudaStream_t aux = nullptr, cap = nullptr;   // boundary-chain stream, capture stream
-  cudaEvent_t fork = nullptr, join = nullptr, ready = nullptr;
+  cudaStream_t aux = nullptr, aux2 = nullptr, cap = nullptr;  // boundary streams, capture
+  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr, ready = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one step, keyed by the buffer parity
   cudaGraph_t gtemplate[2] = {nullptr, nullptr};  // the captured graphs (child graphs of batches)
   bool use_graphs = true;
@@ -219,9 +219,11 @@ static void free_all(lbm_ctx* ctx) {
     if (ctx->gtemplate[k]) cudaGraphDestroy(ctx->gtemplate[k]);
   }
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
+  if (ctx->aux2) cudaStreamDestroy(ctx->aux2);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   if (ctx->fork) cudaEventDestroy(ctx->fork);
   if (ctx->join) cudaEventDestroy(ctx->join);
+  if (ctx->join2) cudaEventDestroy(ctx->join2);
   if (ctx->ready) cudaEventDestroy(ctx->ready);
   for (int k = 0; k < 2; ++k) { cudaFree(ctx->f[k]); cudaFree(ctx->S[k]); }
   cudaFree(ctx->V);
@@ -233,12 +235,16 @@ static void free_all(lbm_ctx* ctx) {
   if (ctx->hflag) cudaFreeHost(ctx->hflag);
 }
 
+static size_t edge_slots(const Geom& g) { return 4 * (size_t)g.ne; }
+
 static void set_roles(lbm_ctx* ctx, int a, int s) {
   Dev& d = ctx->dev;
   d.A = ctx->f[a];
   d.B = ctx->f[1 - a];
   d.Sold = ctx->S[s];
   d.Snew = ctx->S[1 - s];
+  d.Uedge_in = ctx->Uedge + a * edge_slots(ctx->g);
+  d.Uedge_out = ctx->Uedge + (1 - a) * edge_slots(ctx->g);
 }
 
 static lbm_status check_ready(lbm_ctx* ctx) {
@@ -298,7 +304,7 @@ static Geom make_geom(int nx, int ny, const int W[4], int M, int py) {
 static size_t bytes_of(const Geom& g, int q, int es) {
   const size_t max_blocks = (size_t)((g.Lx + 31) / 32) * ((g.Ly + 7) / 8);
   return 2 * (size_t)q * g.plane * es + 2 * (size_t)q * g.Sp * es +
-         sizeof(double) * (16 * (size_t)g.nb + 4 * (size_t)g.ne + 4 * (size_t)g.Lx * g.Ly +
+         sizeof(double) * (16 * (size_t)g.nb + 2 * edge_slots(g) + 4 * (size_t)g.Lx * g.Ly +
                            12 * max_blocks + 16);
 }
 
@@ -401,9 +407,9 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
     }
   }
   if (cudaMalloc(&ctx->V, sizeof(double) * 16 * (size_t)g.nb) != cudaSuccess) return oom("targets");
-  if (cudaMalloc(&ctx->Uedge, sizeof(double) * 4 * (size_t)g.ne) != cudaSuccess) return oom("edges");
+  if (cudaMalloc(&ctx->Uedge, sizeof(double) * 2 * edge_slots(g)) != cudaSuccess) return oom("edges");
   cudaMemset(ctx->V, 0, sizeof(double) * 16 * (size_t)g.nb);
-  cudaMemset(ctx->Uedge, 0, sizeof(double) * 4 * (size_t)g.ne);
+  cudaMemset(ctx->Uedge, 0, sizeof(double) * 2 * edge_slots(g));
   if (cudaMalloc(&ctx->staging, fieldbytes) != cudaSuccess) return oom("staging");
   if (cudaMalloc(&ctx->partials, sizeof(double) * 12 * (size_t)ctx->max_blocks) != cudaSuccess)
     return oom("partials");
@@ -421,23 +427,26 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   int prio_low = 0, prio_high = 0;
   cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
   if (cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&ctx->aux2, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->join2, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ready, cudaEventDisableTiming) != cudaSuccess)
     return oom("streams and events");
   Dev& d = ctx->dev;
   d.g = g;
   d.st = ctx->st;
   d.aux = ctx->aux;
+  d.aux2 = ctx->aux2;
   d.fork = ctx->fork;
   d.join = ctx->join;
+  d.join2 = ctx->join2;
   d.flag = ctx->dflag;
   d.Vtgt = ctx->V;
   d.Va = ctx->V + 4 * (size_t)g.nb;
   d.Vb = ctx->V + 8 * (size_t)g.nb;
   d.Vacc = ctx->V + 12 * (size_t)g.nb;
-  d.Uedge = ctx->Uedge;
   d.bc.bc = (int)bc;
   for (int k = 0; k < 4; ++k) d.bc.edge[k] = bp.edge[k];
   d.bc.beta = bp.beta;
@@ -587,6 +596,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int n) {
         // one stream), so its events measure that class and nothing concurrent
         d.ev = &ctx->prof[(size_t)2 * kKernelClasses * ctx->prof_used++];
         d.aux = nullptr;
+        d.aux2 = nullptr;
       }
       LBM_CK(ctx->ops.step(d, true));
     }
@@ -760,7 +770,9 @@ lbm_status lbm_checkpoint(lbm_ctx* ctx, void* host, size_t bytes) {
   LBM_CK(cudaMemcpyAsync(p, ctx->f[1 - ctx->cur], ctx->fbytes, k, ctx->st)); p += ctx->fbytes;
   if (ctx->sbytes) { LBM_CK(cudaMemcpyAsync(p, ctx->S[ctx->scur], ctx->sbytes, k, ctx->st)); p += ctx->sbytes; }
   LBM_CK(cudaMemcpyAsync(p, ctx->V, sizeof(double) * 4 * ctx->g.nb, k, ctx->st)); p += sizeof(double) * 4 * ctx->g.nb;
-  LBM_CK(cudaMemcpyAsync(p, ctx->Uedge, sizeof(double) * 4 * ctx->g.ne, k, ctx->st));
+  // the edge moments the next step's targets read
+  LBM_CK(cudaMemcpyAsync(p, ctx->Uedge + ctx->cur * edge_slots(ctx->g),
+                         sizeof(double) * edge_slots(ctx->g), k, ctx->st));
   LBM_CK(cudaStreamSynchronize(ctx->st));
   return LBM_OK;
 }
@@ -788,7 +800,7 @@ lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes) {
   LBM_CK(cudaMemcpyAsync(ctx->f[1], p, ctx->fbytes, k, ctx->st)); p += ctx->fbytes;
   if (ctx->sbytes) { LBM_CK(cudaMemcpyAsync(ctx->S[0], p, ctx->sbytes, k, ctx->st)); p += ctx->sbytes; }
   LBM_CK(cudaMemcpyAsync(ctx->V, p, sizeof(double) * 4 * ctx->g.nb, k, ctx->st)); p += sizeof(double) * 4 * ctx->g.nb;
-  LBM_CK(cudaMemcpyAsync(ctx->Uedge, p, sizeof(double) * 4 * ctx->g.ne, k, ctx->st));
+  LBM_CK(cudaMemcpyAsync(ctx->Uedge, p, sizeof(double) * edge_slots(ctx->g), k, ctx->st));
   LBM_CK(cudaStreamSynchronize(ctx->st));
   ctx->steps = h.steps;
   ctx->prev_valid = (h.flags & 1) != 0;

@@ -22,13 +22,18 @@ struct Dev {
   double* Va;        // Runge-Kutta stage buffers [4][nb]
   double* Vb;
   double* Vacc;
-  double* Uedge;     // fluid moments of the outer two layers of F [4][ne]
+  // fluid moments of the outer two layers of F [4][ne], two buffers: the characteristic
+  // targets read the level-n moments (Uedge_in, written by the previous step's frame) while
+  // this step's frame writes the next level's (Uedge_out), so the two can run concurrently
+  const double* Uedge_in;
+  double* Uedge_out;
   int* flag;         // device-visible address of the mapped "unphysical state" flag
   cudaStream_t st;
-  // Boundary-side work (characteristic targets, frame phases, boundary band) runs on aux,
-  // forked from and joined back into st, concurrently with the interior kernel on st.
-  cudaStream_t aux;
-  cudaEvent_t fork, join;
+  // Boundary-side work runs forked from and joined back into st, concurrently with the
+  // interior kernel on st: the characteristic targets and then the boundary band on aux, the
+  // PML frame on aux2 (both may be null: everything then runs in order on st).
+  cudaStream_t aux, aux2;
+  cudaEvent_t fork, join, join2;
   // optional timing: when ev is set, event 2k / 2k+1 are recorded around kernel class k
   // (0 characteristic targets, 1 interior, 2 frame phase 1, 3 frame phase 2, 4 boundary band)
   cudaEvent_t* ev;

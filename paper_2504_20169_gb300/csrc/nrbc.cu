@@ -161,9 +161,9 @@ cudaError_t launch_nrbc_stages(const Dev& d, bool fp32, cudaStream_t s) {
   const int threads = (g.M * kText + 31) / 32 * 32;
   const size_t smem = sizeof(double) * 16 * g.M * kText;
   if (fp32)
-    k_nrbc_rk4<float><<<blocks, threads, smem, s>>>(g, d.bc, d.Uedge, d.Vtgt);
+    k_nrbc_rk4<float><<<blocks, threads, smem, s>>>(g, d.bc, d.Uedge_in, d.Vtgt);
   else
-    k_nrbc_rk4<double><<<blocks, threads, smem, s>>>(g, d.bc, d.Uedge, d.Vtgt);
+    k_nrbc_rk4<double><<<blocks, threads, smem, s>>>(g, d.bc, d.Uedge_in, d.Vtgt);
   return cudaGetLastError();
 }
 

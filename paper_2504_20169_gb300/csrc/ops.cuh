@@ -178,41 +178,44 @@ struct Ops {
     const Consts<Real>& c = consts(d);
     const Real* A = static_cast<const Real*>(d.A);
     Real* B = static_cast<Real*>(d.B);
-    // boundary chain on bs, interior on d.st; both read A and write disjoint parts of B
+    // characteristic targets then boundary band on bs, PML frame on fs, interior on d.st; all
+    // read A and write disjoint parts of B
     const cudaStream_t bs = d.aux ? d.aux : d.st;
+    const cudaStream_t fs = d.aux2 ? d.aux2 : bs;
     auto mark = [&](int k, cudaStream_t s) {
       if (d.ev) cudaEventRecord(d.ev[k], s);
     };
     if (d.aux) {
       cudaEventRecord(d.fork, d.st);
       cudaStreamWaitEvent(d.aux, d.fork, 0);
+      if (d.aux2) cudaStreamWaitEvent(d.aux2, d.fork, 0);
     }
     mark(0, bs);
     if (STREAM && d.bc.bc == 2) launch_nrbc_stages(d, sizeof(Real) == 4, bs);
     mark(1, bs);
-    mark(4, bs);
+    mark(4, fs);
     bool fused = false;
     if constexpr (DEV) {
       if (has_pml(g)) {
         // FP32: single-pass frame (tile + halo in shared memory)
         const FrameTiles ft = make_frame_tiles(g, 256);
         const size_t smem = pml_fused_smem<S>(ft);
-        k_pml_fused<S, STREAM><<<frame_tile_count(ft), 256, smem, bs>>>(
+        k_pml_fused<S, STREAM><<<frame_tile_count(ft), 256, smem, fs>>>(
             g, c, ft, A, B, static_cast<const float*>(d.Sold), static_cast<float*>(d.Snew),
-            d.Uedge, d.bc.bc == 2 ? 1 : 0, d.flag);
+            d.Uedge_out, d.bc.bc == 2 ? 1 : 0, d.flag);
         fused = true;
       }
     }
     if (!fused)
-      k_frame1<S, Real, DEV, STREAM><<<(g.frame_n + 127) / 128, 128, 0, bs>>>(
-          g, c, A, B, static_cast<const Real*>(d.Sold), static_cast<Real*>(d.Snew), d.Uedge,
+      k_frame1<S, Real, DEV, STREAM><<<(g.frame_n + 127) / 128, 128, 0, fs>>>(
+          g, c, A, B, static_cast<const Real*>(d.Sold), static_cast<Real*>(d.Snew), d.Uedge_out,
           d.bc.bc == 2 ? 1 : 0, d.flag);
-    mark(5, bs);
-    mark(6, bs);
+    mark(5, fs);
+    mark(6, fs);
     if (has_pml(g) && !fused)
-      k_frame2<S, Real><<<(g.frame_n + 127) / 128, 128, 0, bs>>>(
+      k_frame2<S, Real><<<(g.frame_n + 127) / 128, 128, 0, fs>>>(
           g, c, B, static_cast<const Real*>(d.Sold), static_cast<const Real*>(d.Snew));
-    mark(7, bs);
+    mark(7, fs);
     mark(8, bs);
     k_gamma<S, Real, DEV, STREAM><<<(g.ngamma + 127) / 128, 128, 0, bs>>>(g, c, d.bc, A, B,
                                                                           d.Vtgt);
@@ -229,6 +232,10 @@ struct Ops {
     if (d.aux) {
       cudaEventRecord(d.join, d.aux);
       cudaStreamWaitEvent(d.st, d.join, 0);
+      if (d.aux2) {
+        cudaEventRecord(d.join2, d.aux2);
+        cudaStreamWaitEvent(d.st, d.join2, 0);
+      }
     }
     if (g.py) {
       const long long n = (long long)(g.Lx + 2 * g.M) * g.M;
