@@ -85,6 +85,11 @@ typedef struct {
   int use_pml_widths;           /* 0: pml_width on every edge; 1: pml_widths below          */
   int pml_widths[4];            /* PML layers on the W, E, S, N edges (0 or 2..4096); thin  */
                                 /* layers away from the outlet (closing remark of Sec. 5)   */
+  int pml_source;               /* bitmask, LBM_BC_NRBC with a PML only: add the PML source */
+                                /* terms I (1), II (2), III (4) of Eq. (NSF-CHAR-PML)       */
+                                /* (Appendix) to the characteristic targets: the moments of  */
+                                /* those parts of Omega^PML at the outermost fluid node      */
+                                /* (0: the characteristic BC of Sec. 4)                      */
   int periodic_y;               /* 1: the y axis is periodic (Sec. 5.1 setting): no S / N    */
                                 /* boundary and no PML there (with use_pml_widths = 0 the    */
                                 /* S / N widths are taken as 0; otherwise they must be 0)    */

@@ -31,6 +31,17 @@ Readings where the paper defers to its ref. [klass-camwa-2024] (not available):
   term untouched, beta = 0 freezes the incoming characteristic. The printed sign is
   available with relax_sign = +1.
 * Corner nodes (outside F along both axes) use the zero-gradient copy.
+
+PML-aware characteristic BC (Appendix, Eq. NSF-CHAR-PML). The PML adds the velocity moments of
+Omega^PML to the conservation laws: terms I (gradient part), II (f_hat part), III (Q part).
+Readings: the source of a band node is the moment of the selected parts of Omega^PML, exactly
+as the discrete collision applies them (Eq. pml-general, per time step), at the nearest fluid
+node x_f (the outermost PML layer, where sigma = sigma_max), with the sign of the collision
+term (a damping; the printed "+" of Eq. NSF-CHAR-PML would amplify); the conserved-variable
+source (mass, momentum, energy = sum f |xi|^2 / 2) is mapped to the primitive variables by the
+exact chain rule at the time-n state of x_f (the printed scaling vector S is its diagonal
+part), and added to dU/dt of every layer of the band, frozen over the Runge-Kutta stages like
+the fluid moments.
 """
 from __future__ import annotations
 
@@ -121,3 +132,15 @@ def tangential(Uline: np.ndarray, periodic: bool = False) -> np.ndarray:
     d[0] = -one_sided(Uline[0], Uline[1], Uline[2])
     d[-1] = one_sided(Uline[-1], Uline[-2], Uline[-3])
     return d
+
+
+def conserved_to_primitive_rate(s_mass, s_mom, s_energy, U):
+    """d(rho, u_x, u_y, T)/dt from d(rho, rho u, E)/dt at state U (..., 4), E = rho (u^2 + D T)/2.
+    d rho = s_m;  rho du = s_mom - u s_m;  (D/2) rho dT = s_E - u . s_mom + (u^2/2 - (D/2) T) s_m."""
+    rho, ux, uy, T = U[..., 0], U[..., 1], U[..., 2], U[..., 3]
+    u2 = ux * ux + uy * uy
+    dux = (s_mom[0] - ux * s_mass) / rho
+    duy = (s_mom[1] - uy * s_mass) / rho
+    dT = (s_energy - ux * s_mom[0] - uy * s_mom[1] + (0.5 * u2 - 0.5 * D * T) * s_mass) \
+        / (0.5 * D * rho)
+    return np.stack([s_mass, dux, duy, dT], axis=-1)

@@ -146,6 +146,17 @@ def gradient(Q: np.ndarray, periodic_y: bool = False):
     return gx, gy
 
 
+def omega_pml_terms(e: np.ndarray, gx, gy, fhat, Q, sigma_x, sigma_y=None):
+    """The three parts of Eq. (pml-general), each (q, Ly, Lx): the gradient part
+    -(sigma_y c_x dQ/dx + sigma_x c_y dQ/dy), the f_hat part -(sigma_x + sigma_y) f_hat and the
+    Q part -sigma_x sigma_y Q (their moments are the terms I, II, III of Eq. NSF-CHAR-PML)."""
+    sigma_y = sigma_x if sigma_y is None else sigma_y
+    ex = e[:, 0].astype(np.float64).reshape(-1, 1, 1)
+    ey = e[:, 1].astype(np.float64).reshape(-1, 1, 1)
+    return (-(sigma_y * ex * gx + sigma_x * ey * gy), -(sigma_x + sigma_y) * fhat,
+            -(sigma_x * sigma_y) * Q)
+
+
 def omega_pml(e: np.ndarray, gx, gy, fhat, Q, sigma_x, sigma_y=None):
     """Eq. (pml-general), shape (q, Ly, Lx):
     -(sigma_y c_x dQ/dx + sigma_x c_y dQ/dy + (sigma_x + sigma_y) f_hat + sigma_x sigma_y Q);

@@ -41,11 +41,14 @@ EDGES = ("W", "E", "S", "N")
 class OracleLBM:
     def __init__(self, nx, ny, W, tau, sigma_max=0.0, sigma_power=2, bc="zg", q=37,
                  nrbc_edges=(0, 0, 0, 0), beta=0.0, mean=(1.0, 0.0, 0.0, 1.0),
-                 relax_sign=-1.0, pml_on=True, Wy=None, periodic_y=False, sigma_split=False):
+                 relax_sign=-1.0, pml_on=True, Wy=None, periodic_y=False, sigma_split=False,
+                 pml_source=0):
         """W: PML layers on every edge, or on the W and E edges when Wy (S and N edges) is
         given, or a per-edge tuple (W_w, W_e, W_s, W_n). periodic_y: the y axis wraps (no PML
         on it; Wy defaults to 0 then); the x edges keep the chosen BC. sigma_split: the
-        general sigma_x != sigma_y form of Eq. (pml-general) instead of sigma_x = sigma_y."""
+        general sigma_x != sigma_y form of Eq. (pml-general) instead of sigma_x = sigma_y.
+        pml_source: bitmask of the PML source terms I (1), II (2), III (4) of Eq. NSF-CHAR-PML
+        added to the characteristic targets (Appendix; 0 = the characteristic BC of Sec. 4)."""
         self.lat = lattice(q)
         self.pml_on = pml_on
         self.periodic_y = bool(periodic_y)
@@ -65,6 +68,8 @@ class OracleLBM:
         self.tau = tau
         self.bc = bc
         self.nrbc_edges = tuple(nrbc_edges)
+        self.pml_source = int(pml_source)
+        self._src = None
         self.beta = beta
         self.relax_sign = relax_sign
         M, Lx, Ly = self.M, self.Lx, self.Ly
@@ -132,6 +137,16 @@ class OracleLBM:
             # columns included (those hold the x-edge boundary values just set)
             f[:] = f[:, self._wry, :]
 
+    def _edge_sources(self, om, Uf):
+        """Primitive-variable PML sources (Appendix) at the outermost fluid node of every band
+        position: edge -> (m, 4), from the selected parts om (q, Ly, Lx) of Omega^PML."""
+        xi = self.lat.xi
+        mass = om.sum(axis=0)
+        mom = np.tensordot(xi.T, om, axes=(1, 0))                          # (2, Ly, Lx)
+        energy = 0.5 * np.tensordot((xi ** 2).sum(1), om, axes=(0, 0))
+        prim = ch.conserved_to_primitive_rate(mass, mom, energy, Uf)     # (Ly, Lx, 4)
+        return {"W": prim[:, 0], "E": prim[:, -1], "S": prim[0, :], "N": prim[-1, :]}
+
     def _target_rates(self, V, U):
         """dU/dt of every edge-band node for the boundary state V (dict edge -> M layers of
         (m, 4) arrays) and the time-n fluid moments U (Ly, Lx, 4) on F."""
@@ -159,8 +174,11 @@ class OracleLBM:
                 U0 = V[edge][j - 1]
                 dUn = out * ch.one_sided(U0, U_at(j - 1), U_at(j - 2))
                 dUt = ch.tangential(U0, periodic=self.periodic_y and axis == 0)
-                layers.append(ch.rate(U0, dUn, dUt, axis, out, self.nrbc_edges[k], self.beta,
-                                      self.lat.r, self.relax_sign))
+                rt = ch.rate(U0, dUn, dUt, axis, out, self.nrbc_edges[k], self.beta,
+                             self.lat.r, self.relax_sign)
+                if self._src is not None:
+                    rt = rt + self._src[edge]                                # Appendix source
+                layers.append(rt)
             rates[edge] = layers
         return rates
 
@@ -201,6 +219,7 @@ class OracleLBM:
         self.f = f
         self.Q = None
         self.fhat_prev = None
+        self._src = None
         self.step_count = 0
 
     def step(self, n=1):
@@ -222,6 +241,13 @@ class OracleLBM:
                 gx, gy = pml.gradient(Q, self.periodic_y)                    # 4
                 om = pml.omega_pml(lat.e, gx, gy, fhat, Q, self.sigma_x, self.sigma_y)
                 fstar[Fs] = fstar[Fs] + np.where(self.in_P, om, 0.0)         # 5 (PML part)
+                if self.bc == "nrbc" and self.pml_source:
+                    parts = pml.omega_pml_terms(lat.e, gx, gy, fhat, Q, self.sigma_x,
+                                                self.sigma_y)
+                    sel = sum(pt for k, pt in enumerate(parts) if self.pml_source >> k & 1)
+                    M = self.M
+                    Uf = np.stack([rho, u[0], u[1], T], axis=-1)[M:M + self.Ly, M:M + self.Lx]
+                    self._src = self._edge_sources(np.where(self.in_P, sel, 0.0), Uf)
             if self.periodic_y:
                 # the rows beyond a periodic y axis carry the post-collision populations of
                 # the rows they image (PML term included), as on an unbounded periodic lattice

@@ -178,6 +178,7 @@ struct lbm_ctx {
   void* S[2] = {nullptr, nullptr};
   double* V = nullptr;        // 4 arrays of [4][nb]: targets, stage a, stage b, accumulator
   double* Uedge = nullptr;    // two buffers of [4][ne] (ping-pong with the populations)
+  double* Sedge = nullptr;    // two buffers of [4][2 (Lx + Ly)]: Appendix PML source
   double* staging = nullptr;  // [4][Lx*Ly]
   double* partials = nullptr;
   int max_blocks = 0;
@@ -228,6 +229,7 @@ static void free_all(lbm_ctx* ctx) {
   for (int k = 0; k < 2; ++k) { cudaFree(ctx->f[k]); cudaFree(ctx->S[k]); }
   cudaFree(ctx->V);
   cudaFree(ctx->Uedge);
+  cudaFree(ctx->Sedge);
   cudaFree(ctx->staging);
   cudaFree(ctx->partials);
   cudaFree(ctx->dout);
@@ -236,6 +238,7 @@ static void free_all(lbm_ctx* ctx) {
 }
 
 static size_t edge_slots(const Geom& g) { return 4 * (size_t)g.ne; }
+static size_t source_slots(const Geom& g) { return 4 * 2 * ((size_t)g.Lx + g.Ly); }
 
 static void set_roles(lbm_ctx* ctx, int a, int s) {
   Dev& d = ctx->dev;
@@ -245,6 +248,8 @@ static void set_roles(lbm_ctx* ctx, int a, int s) {
   d.Snew = ctx->S[1 - s];
   d.Uedge_in = ctx->Uedge + a * edge_slots(ctx->g);
   d.Uedge_out = ctx->Uedge + (1 - a) * edge_slots(ctx->g);
+  d.Sedge_in = ctx->Sedge + a * source_slots(ctx->g);
+  d.Sedge_out = ctx->Sedge + (1 - a) * source_slots(ctx->g);
 }
 
 static lbm_status check_ready(lbm_ctx* ctx) {
@@ -304,7 +309,8 @@ static Geom make_geom(int nx, int ny, const int W[4], int M, int py) {
 static size_t bytes_of(const Geom& g, int q, int es) {
   const size_t max_blocks = (size_t)((g.Lx + 31) / 32) * ((g.Ly + 7) / 8);
   return 2 * (size_t)q * g.plane * es + 2 * (size_t)q * g.Sp * es +
-         sizeof(double) * (16 * (size_t)g.nb + 2 * edge_slots(g) + 4 * (size_t)g.Lx * g.Ly +
+         sizeof(double) * (16 * (size_t)g.nb + 2 * edge_slots(g) + 2 * source_slots(g) +
+                           4 * (size_t)g.Lx * g.Ly +
                            12 * max_blocks + 16);
 }
 
@@ -355,6 +361,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
     return fail("periodic mode has no PML");
   if (bp.periodic_y && (W4[2] || W4[3])) return fail("a periodic y axis has no PML");
   if (bp.periodic_y && bc == LBM_BC_PERIODIC) return fail("periodic_y needs a ZG or NRBC x edge");
+  if (bp.pml_source < 0 || bp.pml_source > 7) return fail("pml_source is a bitmask of 1, 2, 4");
   if (!(bp.rho0 > 0) || !(bp.T0 > 0) || !std::isfinite(bp.u0x) || !std::isfinite(bp.u0y) ||
       !std::isfinite(bp.beta))
     return fail("bad mean state or beta");
@@ -410,6 +417,9 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   if (cudaMalloc(&ctx->Uedge, sizeof(double) * 2 * edge_slots(g)) != cudaSuccess) return oom("edges");
   cudaMemset(ctx->V, 0, sizeof(double) * 16 * (size_t)g.nb);
   cudaMemset(ctx->Uedge, 0, sizeof(double) * 2 * edge_slots(g));
+  if (cudaMalloc(&ctx->Sedge, sizeof(double) * 2 * source_slots(g)) != cudaSuccess)
+    return oom("PML source");
+  cudaMemset(ctx->Sedge, 0, sizeof(double) * 2 * source_slots(g));
   if (cudaMalloc(&ctx->staging, fieldbytes) != cudaSuccess) return oom("staging");
   if (cudaMalloc(&ctx->partials, sizeof(double) * 12 * (size_t)ctx->max_blocks) != cudaSuccess)
     return oom("partials");
@@ -451,6 +461,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   for (int k = 0; k < 4; ++k) d.bc.edge[k] = bp.edge[k];
   d.bc.beta = bp.beta;
   d.bc.relax_sign = bp.relax_sign == 0.0 ? -1.0 : bp.relax_sign;
+  d.bc.pml_source = bp.pml_source;
   d.bc.r = ctx->r;
   d.bc.inv_r = 1.0 / ctx->r;
   d.bc.omega = ctx->omega;
@@ -735,7 +746,7 @@ lbm_status lbm_profile_read(lbm_ctx* ctx, double* ms, int* steps) {
 }
 
 // checkpoint layout: header of 8 int64, then current and previous population buffers, the PML
-// accumulator of the current level, the targets and the saved edge moments
+// accumulator of the current level, the targets, the saved edge moments and PML sources
 struct CkptHeader { int64_t magic, q, nx, ny, widths, prec, steps, flags; };
 
 // the four PML widths (each <= 4096) packed 16 bits apiece, and the sigma form
@@ -748,7 +759,7 @@ static const int64_t kMagic = 0x4c424d434b505431ll;
 lbm_status lbm_checkpoint_size(const lbm_ctx* ctx, size_t* bytes) {
   if (!ctx || !bytes) return LBM_EINVAL;
   *bytes = sizeof(CkptHeader) + 2 * ctx->fbytes + ctx->sbytes +
-           sizeof(double) * (4 * (size_t)ctx->g.nb + 4 * (size_t)ctx->g.ne);
+           sizeof(double) * (4 * (size_t)ctx->g.nb + edge_slots(ctx->g) + source_slots(ctx->g));
   return LBM_OK;
 }
 
@@ -773,6 +784,9 @@ lbm_status lbm_checkpoint(lbm_ctx* ctx, void* host, size_t bytes) {
   // the edge moments the next step's targets read
   LBM_CK(cudaMemcpyAsync(p, ctx->Uedge + ctx->cur * edge_slots(ctx->g),
                          sizeof(double) * edge_slots(ctx->g), k, ctx->st));
+  p += sizeof(double) * edge_slots(ctx->g);
+  LBM_CK(cudaMemcpyAsync(p, ctx->Sedge + ctx->cur * source_slots(ctx->g),
+                         sizeof(double) * source_slots(ctx->g), k, ctx->st));
   LBM_CK(cudaStreamSynchronize(ctx->st));
   return LBM_OK;
 }
@@ -801,6 +815,8 @@ lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes) {
   if (ctx->sbytes) { LBM_CK(cudaMemcpyAsync(ctx->S[0], p, ctx->sbytes, k, ctx->st)); p += ctx->sbytes; }
   LBM_CK(cudaMemcpyAsync(ctx->V, p, sizeof(double) * 4 * ctx->g.nb, k, ctx->st)); p += sizeof(double) * 4 * ctx->g.nb;
   LBM_CK(cudaMemcpyAsync(ctx->Uedge, p, sizeof(double) * edge_slots(ctx->g), k, ctx->st));
+  p += sizeof(double) * edge_slots(ctx->g);
+  LBM_CK(cudaMemcpyAsync(ctx->Sedge, p, sizeof(double) * source_slots(ctx->g), k, ctx->st));
   LBM_CK(cudaStreamSynchronize(ctx->st));
   ctx->steps = h.steps;
   ctx->prev_valid = (h.flags & 1) != 0;

@@ -63,6 +63,7 @@ struct BcParams {
   int bc;            // 0 periodic, 1 zero gradient, 2 characteristic
   int edge[4];       // W E S N: 0 PNR-LODI, 1 CBC relax
   double beta, relax_sign, r, omega, inv_r;
+  int pml_source;    // bitmask of the Appendix PML source terms I (1), II (2), III (4)
 };
 
 __host__ __device__ inline long long gindex(const Geom& g, int x, int y) {
@@ -367,6 +368,33 @@ __device__ inline void save_edge_moments(const Geom& g, double* Ue, int x, int y
   if (y >= Ly - 2) put(4 * Ly + 2 * Lx + (Ly - 1 - y) * Lx + x);
 }
 
+// Slot of the outermost fluid node (x, y) in the PML-source arrays of edge e (W E S N):
+// W [Ly], E [Ly], S [Lx], N [Lx]; -1 when the node is not on that edge.
+__device__ inline int src_slot(const Geom& g, int e, int x, int y) {
+  if (e == 0) return x == 0 ? y : -1;
+  if (e == 1) return x == g.Lx - 1 ? g.Ly + y : -1;
+  if (g.py) return -1;
+  if (e == 2) return y == 0 ? 2 * g.Ly + x : -1;
+  return y == g.Ly - 1 ? 2 * g.Ly + g.Lx + x : -1;
+}
+
+// Mass, momentum and energy moments (sum of |xi|^2 / 2) of a per-direction PML part, written
+// (add = false) or added (add = true) into every edge slot of an outermost fluid node.
+template <class Real>
+__device__ inline void put_pml_source(const Geom& g, double* Se, int x, int y, const Real mom[4],
+                                      bool add) {
+  const int ns = 2 * (g.Lx + g.Ly);
+  for (int e = 0; e < 4; ++e) {
+    const int k = src_slot(g, e, x, y);
+    if (k < 0) continue;
+    for (int q = 0; q < 4; ++q) Se[q * ns + k] = (add ? Se[q * ns + k] : 0.0) + double(mom[q]);
+  }
+}
+
+__device__ inline bool outermost(const Geom& g, int x, int y) {
+  return x == 0 || x == g.Lx - 1 || (!g.py && (y == 0 || y == g.Ly - 1));
+}
+
 // Frame, phase 1: BGK plus, on P and its inner ring, the trapezoidal accumulator
 // S = Q + f_hat / 2 (Eq. PMLQ: Q^n = S^(n-1) + f_hat^n / 2, S^n = S^(n-1) + f_hat^n), and on P
 // the local part -((sigma_x + sigma_y) f_hat + sigma_x sigma_y Q) of Eq. (pml-general)
@@ -375,7 +403,7 @@ template <class S, class Real, bool DEV, bool STREAM>
 __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Real* __restrict__ A,
                                                 Real* __restrict__ B, const Real* __restrict__ Sold,
                                                 Real* __restrict__ Snew, double* Uedge, int save_edges,
-                                                int* flag) {
+                                                int* flag, double* Sedge, int src_mask) {
   const int fi = blockIdx.x * blockDim.x + threadIdx.x;
   if (fi >= g.frame_n) return;
   int x, y;
@@ -394,6 +422,10 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
   if (in_p) pml_sigmas(c, pn, sx, sy);
   const Real ssum = sx + sy, sprod = sx * sy;
   const EqCoef<Real> k = eq_coef<S::ORDER, Real>(m);
+  // Appendix PML source at the outermost layer: moments of the f_hat (II) and Q (III) parts
+  // here; the gradient part (I) is added by k_frame2
+  const bool src = src_mask && outermost(g, x, y);
+  Real smom[4] = {Real(0), Real(0), Real(0), Real(0)};
   if (has_q) {
     // all accumulator loads in flight before any store
     Real so[S::Q];
@@ -408,11 +440,26 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
       Real out = p[i] + c.omega * (eq - p[i]);
       if (in_p) out = out - (ssum * fhat + sprod * q);
       B[(long long)i * g.plane + idx] = out;
+      if (src && in_p) {
+        const Real part = -(((src_mask & 2) ? ssum * fhat : Real(0)) +
+                            ((src_mask & 4) ? sprod * q : Real(0)));
+        smom[0] += part;
+        smom[1] += Real(S::ex(i)) * part;
+        smom[2] += Real(S::ey(i)) * part;
+        smom[3] += Real(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
+      }
     }
   } else {
     collide_bgk<S, Real, DEV>(p, m, c);
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) B[(long long)i * g.plane + idx] = p[i];
+  }
+  if (src) {
+    // lattice moments -> physical: xi = r e, |xi|^2 / 2 = r^2 |e|^2 / 2
+    smom[1] *= c.r;
+    smom[2] *= c.r;
+    smom[3] *= Real(0.5) * c.r2;
+    put_pml_source(g, Sedge, x, y, smom, false);
   }
 }
 
@@ -422,7 +469,8 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
 template <class S, class Real>
 __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __restrict__ B,
                                                 const Real* __restrict__ Sold,
-                                                const Real* __restrict__ Snew) {
+                                                const Real* __restrict__ Snew, double* Sedge,
+                                                int src_mask) {
   const int fi = blockIdx.x * blockDim.x + threadIdx.x;
   if (fi >= g.frame_n) return;
   int x, y;
@@ -462,6 +510,8 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
     cy0 = Real(0.5); cy1 = Real(-0.5); cy2 = Real(0);
   }
   const long long idx = gindex(g, x, y);
+  const bool src = (src_mask & 1) && outermost(g, x, y);   // Appendix term I
+  Real smom[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) {
     const Real* so = Sold + (long long)i * g.Sp;
@@ -481,6 +531,19 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
     }
     Real* b = B + (long long)i * g.plane + idx;
     *b = *b - Real(0.5) * gq;   // Q = (S^(n-1) + S^n) / 2
+    if (src) {
+      const Real part = -Real(0.5) * gq;
+      smom[0] += part;
+      smom[1] += Real(S::ex(i)) * part;
+      smom[2] += Real(S::ey(i)) * part;
+      smom[3] += Real(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
+    }
+  }
+  if (src) {
+    smom[1] *= c.r;
+    smom[2] *= c.r;
+    smom[3] *= Real(0.5) * c.r2;
+    put_pml_source(g, Sedge, x, y, smom, true);
   }
 }
 

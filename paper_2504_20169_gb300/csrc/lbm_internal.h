@@ -27,6 +27,10 @@ struct Dev {
   // this step's frame writes the next level's (Uedge_out), so the two can run concurrently
   const double* Uedge_in;
   double* Uedge_out;
+  // Appendix PML source (mass, momentum, energy rates) at the outermost fluid node of every
+  // edge position [4][2 (Lx + Ly)], double-buffered like Uedge
+  const double* Sedge_in;
+  double* Sedge_out;
   int* flag;         // device-visible address of the mapped "unphysical state" flag
   cudaStream_t st;
   // Boundary-side work runs forked from and joined back into st, concurrently with the

@@ -68,7 +68,7 @@ constexpr int kChunk = 32, kHalo = 4, kText = kChunk + 2 * kHalo;
 
 template <class R>
 __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
-                           double* __restrict__ Vg) {
+                           const double* __restrict__ Se, double* __restrict__ Vg) {
   const int M = g.M, Lx = g.Lx, Ly = g.Ly;
   const int cw = (Ly + kChunk - 1) / kChunk, cs = (Lx + kChunk - 1) / kChunk;
   int e, k = blockIdx.x;
@@ -113,6 +113,21 @@ __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
     return load_prim(Ue, g.ne, ueoff + layer * len + wr(tt), xaxis);
   };
   const int variant = bc.edge[e];
+  // Appendix PML source of this band position, mapped to (rho, u_x, u_y, T) rates at the
+  // time-n state of the outermost fluid node: d rho = s_m, rho du = s_mom - u s_m,
+  // (D/2) rho dT = s_E - u . s_mom + (u^2/2 - (D/2) T) s_m (D = 2); constant over the stages
+  double src[4] = {0, 0, 0, 0};
+  if (bc.pml_source && live) {
+    const int ns = 2 * (Lx + Ly);
+    const int sb = (e == 0 ? 0 : e == 1 ? Ly : e == 2 ? 2 * Ly : 2 * Ly + Lx) + wr(t);
+    const int ub = ueoff + wr(t);
+    const double rho = Ue[ub], ux = Ue[g.ne + ub], uy = Ue[2 * g.ne + ub], T = Ue[3 * g.ne + ub];
+    const double sm = Se[sb], sx = Se[ns + sb], sy = Se[2 * ns + sb], sE = Se[3 * ns + sb];
+    src[0] = sm;
+    src[1] = (sx - ux * sm) / rho;
+    src[2] = (sy - uy * sm) / rho;
+    src[3] = (sE - ux * sx - uy * sy + (0.5 * (ux * ux + uy * uy) - T) * sm) / rho;
+  }
   double kk[4] = {0, 0, 0, 0};
   for (int s = 1; s <= 4; ++s) {
     const int in_buf = s == 1 ? 0 : (s == 3 ? 2 : 1);  // V0, a, b, a
@@ -133,6 +148,7 @@ __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
         Vc = prim(in_buf, j, ta + 2);
       }
       char_rate<R>(bc, variant, out, U0, U1, U2, Va, Vb, Vc, ca, cb, cc, xaxis, kk);
+      for (int q = 0; q < 4; ++q) kk[q] += src[q];
     }
     __syncthreads();   // everyone has read the stage input before it is overwritten
     if (live && t >= slo && t < shi) {
@@ -161,9 +177,9 @@ cudaError_t launch_nrbc_stages(const Dev& d, bool fp32, cudaStream_t s) {
   const int threads = (g.M * kText + 31) / 32 * 32;
   const size_t smem = sizeof(double) * 16 * g.M * kText;
   if (fp32)
-    k_nrbc_rk4<float><<<blocks, threads, smem, s>>>(g, d.bc, d.Uedge_in, d.Vtgt);
+    k_nrbc_rk4<float><<<blocks, threads, smem, s>>>(g, d.bc, d.Uedge_in, d.Sedge_in, d.Vtgt);
   else
-    k_nrbc_rk4<double><<<blocks, threads, smem, s>>>(g, d.bc, d.Uedge_in, d.Vtgt);
+    k_nrbc_rk4<double><<<blocks, threads, smem, s>>>(g, d.bc, d.Uedge_in, d.Sedge_in, d.Vtgt);
   return cudaGetLastError();
 }
 

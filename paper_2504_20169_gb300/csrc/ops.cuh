@@ -190,6 +190,8 @@ struct Ops {
       cudaStreamWaitEvent(d.aux, d.fork, 0);
       if (d.aux2) cudaStreamWaitEvent(d.aux2, d.fork, 0);
     }
+    // Appendix PML source terms: only with a characteristic BC and a PML
+    const int src_mask = (d.bc.bc == 2 && has_pml(g)) ? d.bc.pml_source : 0;
     mark(0, bs);
     if (STREAM && d.bc.bc == 2) launch_nrbc_stages(d, sizeof(Real) == 4, bs);
     mark(1, bs);
@@ -202,19 +204,20 @@ struct Ops {
         const size_t smem = pml_fused_smem<S>(ft);
         k_pml_fused<S, STREAM><<<frame_tile_count(ft), 256, smem, fs>>>(
             g, c, ft, A, B, static_cast<const float*>(d.Sold), static_cast<float*>(d.Snew),
-            d.Uedge_out, d.bc.bc == 2 ? 1 : 0, d.flag);
+            d.Uedge_out, d.bc.bc == 2 ? 1 : 0, d.flag, d.Sedge_out, src_mask);
         fused = true;
       }
     }
     if (!fused)
       k_frame1<S, Real, DEV, STREAM><<<(g.frame_n + 127) / 128, 128, 0, fs>>>(
           g, c, A, B, static_cast<const Real*>(d.Sold), static_cast<Real*>(d.Snew), d.Uedge_out,
-          d.bc.bc == 2 ? 1 : 0, d.flag);
+          d.bc.bc == 2 ? 1 : 0, d.flag, d.Sedge_out, src_mask);
     mark(5, fs);
     mark(6, fs);
     if (has_pml(g) && !fused)
       k_frame2<S, Real><<<(g.frame_n + 127) / 128, 128, 0, fs>>>(
-          g, c, B, static_cast<const Real*>(d.Sold), static_cast<const Real*>(d.Snew));
+          g, c, B, static_cast<const Real*>(d.Sold), static_cast<const Real*>(d.Snew),
+          d.Sedge_out, src_mask);
     mark(7, fs);
     mark(8, bs);
     k_gamma<S, Real, DEV, STREAM><<<(g.ngamma + 127) / 128, 128, 0, bs>>>(g, c, d.bc, A, B,

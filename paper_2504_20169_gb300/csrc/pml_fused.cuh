@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
                                                    float* __restrict__ B,
                                                    const float* __restrict__ Sold,
                                                    float* __restrict__ Snew, double* Uedge,
-                                                   int save_edges, int* flag) {
+                                                   int save_edges, int* flag, double* Sedge,
+                                                   int src_mask) {
   extern __shared__ float smem[];
   // ---- tile of this block
   int x0, y0, tw, th, band;  // band 0 bottom, 1 top, 2 left, 3 right
@@ -182,6 +183,9 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   else if (!g.py && y == g.Ly - 1) {
     cy0 = 1.5f; cy1 = -2.f; cy2 = 0.5f; oy0 = 0; oy1 = -ew; oy2 = -2 * ew;
   }
+  // Appendix PML source at the outermost layer: moments of the selected parts of Omega^PML
+  const bool src = src_mask && outermost(g, x, y);
+  float smom[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) {
     const float eq = eq_dir<S, float, true>(i, m, kc, c);
@@ -195,8 +199,22 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
       if (S::ex(i) != 0) gq += sy * float(S::ex(i)) * (cx0 * q[ox0] + cx1 * q[ox1] + cx2 * q[ox2]);
       if (S::ey(i) != 0) gq += sx * float(S::ey(i)) * (cy0 * q[oy0] + cy1 * q[oy1] + cy2 * q[oy2]);
       out = out - (gq + ssum * fhat + sprod * qn);
+      if (src) {
+        const float part = -(((src_mask & 1) ? gq : 0.f) + ((src_mask & 2) ? ssum * fhat : 0.f) +
+                             ((src_mask & 4) ? sprod * qn : 0.f));
+        smom[0] += part;
+        smom[1] += float(S::ex(i)) * part;
+        smom[2] += float(S::ey(i)) * part;
+        smom[3] += float(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
+      }
     }
     B[(long long)i * g.plane + idx] = out;
+  }
+  if (src) {
+    smom[1] *= c.r;
+    smom[2] *= c.r;
+    smom[3] *= 0.5f * c.r2;
+    put_pml_source(g, Sedge, x, y, smom, false);
   }
 }
 

@@ -171,6 +171,33 @@ def test_parity_split_sigma(widths, bc, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+@pytest.mark.parametrize("src,case", [(1, "pulse"), (7, "pulse"), (1, "step"), (2, "step"),
+                                      (5, "split")])
+def test_parity_pml_aware_characteristic_bc(src, case, precision):
+    """Appendix, Eq. (NSF-CHAR-PML): the moments of the selected parts of Omega^PML at the
+    outermost fluid node added to the characteristic targets (terms I, II, III as a bitmask):
+    a 2-D pulse with CBC relax / PNR-LODI edges, the Sec. 5.1 density step with W = 10 on a
+    periodic y axis, and per-edge widths with the split sigma form."""
+    if case == "pulse":
+        nx, ny, W = 40, 36, 6
+        kw = case_kwargs(nx=nx, ny=ny, W=W, tau=0.75, sigma_max=0.1, sigma_power=2, bc="nrbc",
+                         nrbc_edges=(0, 1, 0, 1), beta=0.2, mean=(1.0, 0.05, 0.0, 1.0),
+                         pml_source=src)
+        fields = wl.pressure_pulse(nx, ny, W, amp=2e-3, halfwidth=4.0, u0=(0.05, 0.0))
+    elif case == "step":
+        nx, ny, W = 60, 12, 10
+        kw = case_kwargs(nx=nx, ny=ny, W=W, tau=0.8, sigma_max=0.05, sigma_power=2, bc="nrbc",
+                         mean=(1.0, 0.05, 0.0, 1.0), periodic_y=True, pml_source=src)
+        fields = wl.density_step(nx, ny, Ma=0.05, W=W, Wy=0)
+    else:
+        nx, ny, widths = 38, 30, (4, 9, 3, 6)
+        kw = case_kwargs(nx=nx, ny=ny, W=0, tau=0.75, sigma_max=0.15, sigma_power=2, bc="nrbc",
+                         mean=(1.0, 0.04, 0.0, 1.0), widths=widths, split=True, pml_source=src)
+        fields = wl.random_smooth_state(nx, ny, widths, seed=5, du=0.03, mean_u=(0.04, 0.0))
+    check(kw, fields, 40, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
 @pytest.mark.parametrize("q", [17, 9])
 @pytest.mark.parametrize("bc", ["zg", "nrbc"])
 def test_parity_other_stencils(q, bc, precision):

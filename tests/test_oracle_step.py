@@ -318,13 +318,13 @@ def test_split_x_slab_ignores_the_x_gradient(monkeypatch):
     assert np.abs(run(False) - base[False]).max() > 1e-9
 
 
-@pytest.mark.parametrize("split", [False, True])
-def test_per_edge_widths_mirror(split):
+@pytest.mark.parametrize("split,src", [(False, 0), (True, 0), (False, 7), (True, 1)])
+def test_per_edge_widths_mirror(split, src):
     """Widths (W_w, W_e) = (3, 7) and the x-mirrored problem with (7, 3): mirrored results
-    (catches a width or a layer fraction taken from the wrong edge)."""
+    (catches a width, a layer fraction or an Appendix PML source taken from the wrong edge)."""
     nx, ny = 26, 20
-    a = OracleLBM(nx, ny, (3, 7, 4, 2), 0.7, 0.1, 2, "nrbc", sigma_split=split)
-    b = OracleLBM(nx, ny, (7, 3, 4, 2), 0.7, 0.1, 2, "nrbc", sigma_split=split)
+    a = OracleLBM(nx, ny, (3, 7, 4, 2), 0.7, 0.1, 2, "nrbc", sigma_split=split, pml_source=src)
+    b = OracleLBM(nx, ny, (7, 3, 4, 2), 0.7, 0.1, 2, "nrbc", sigma_split=split, pml_source=src)
     c = (9.0, 8.0)
     a.init(*wl.pressure_pulse(nx, ny, (3, 7, 4, 2), amp=1e-3, halfwidth=3.0, center=c))
     b.init(*wl.pressure_pulse(nx, ny, (7, 3, 4, 2), amp=1e-3, halfwidth=3.0,
@@ -347,3 +347,46 @@ def test_density_step_profile():
     assert r[49] == pytest.approx(1.025) and r[149] == pytest.approx(1.025)
     assert np.abs(np.diff(r)).max() < 0.05 * 0.5 / 2 + 1e-12     # no jump anywhere
     assert np.all(ux == 0.05) and np.all(uy == 0.0) and np.all(T == 1.0)
+
+
+def test_conserved_to_primitive_rate_is_the_derivative_of_the_variable_map():
+    """Appendix source mapping: d(rho, u, T) from d(rho, rho u, E) equals the derivative of
+    u = m / rho, T = (2 E / rho - u^2) / D along the same conserved perturbation."""
+    rng = np.random.default_rng(3)
+    U = np.column_stack([1 + 0.1 * rng.random(5), 0.2 * rng.standard_normal(5),
+                         0.2 * rng.standard_normal(5), 1 + 0.1 * rng.random(5)])
+
+    def cons(U):
+        rho, ux, uy, T = U.T
+        return np.column_stack([rho, rho * ux, rho * uy, 0.5 * rho * (ux * ux + uy * uy + 2 * T)])
+
+    def prim(C):
+        rho, mx, my, E = C.T
+        ux, uy = mx / rho, my / rho
+        return np.column_stack([rho, ux, uy, (2 * E / rho - ux * ux - uy * uy) / 2])
+
+    dC = rng.standard_normal((5, 4))
+    h = 1e-6
+    fd = (prim(cons(U) + h * dC) - prim(cons(U) - h * dC)) / (2 * h)
+    got = ch.conserved_to_primitive_rate(dC[:, 0], dC[:, 1:3].T, dC[:, 3], U)
+    assert np.max(np.abs(got - fd)) < 1e-8
+
+
+def test_pml_source_first_step_closed_form():
+    """Appendix term II at the first step from a uniform density excess delta at rest (Q^0 = 0,
+    so terms I and III vanish): the outermost PML layer (sigma = sigma_max) gets
+    d rho / dt = -2 sigma_max delta (the mass moment of -2 sigma f_hat), du = dT = 0; term I
+    alone gives zero."""
+    nx, W, s, d = 16, 6, 0.05, 1e-3
+    for src, want in ((2, -2.0 * s * d), (1, 0.0), (7, -2.0 * s * d)):
+        o = OracleLBM(nx, nx, W, 0.7, s, 2, "nrbc", pml_source=src)
+        o.init(*wl.uniform(nx, nx, W, rho=1.0 + d))
+        o.step(1)
+        for edge in ("W", "E", "S", "N"):
+            v = o._src[edge]
+            assert np.allclose(v[:, 0], want, rtol=1e-12, atol=1e-18), (src, edge)
+            assert np.abs(v[:, 1:]).max() < 1e-16
+    o = OracleLBM(nx, nx, W, 0.7, s, 2, "nrbc")
+    o.init(*wl.uniform(nx, nx, W, rho=1.0 + d))
+    o.step(1)
+    assert o._src is None
