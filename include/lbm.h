@@ -89,7 +89,9 @@ typedef struct {
                                 /* terms I (1), II (2), III (4) of Eq. (NSF-CHAR-PML)       */
                                 /* (Appendix) to the characteristic targets: the moments of  */
                                 /* those parts of Omega^PML at the outermost fluid node      */
-                                /* (0: the characteristic BC of Sec. 4)                      */
+                                /* (0: the characteristic BC of Sec. 4); adding 8 takes the  */
+                                /* "+" printed in Eq. (NSF-CHAR-PML) instead of the sign of  */
+                                /* the collision term                                        */
   int periodic_y;               /* 1: the y axis is periodic (Sec. 5.1 setting): no S / N    */
                                 /* boundary and no PML there (with use_pml_widths = 0 the    */
                                 /* S / N widths are taken as 0; otherwise they must be 0)    */

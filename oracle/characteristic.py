@@ -37,7 +37,7 @@ Omega^PML to the conservation laws: terms I (gradient part), II (f_hat part), II
 Readings: the source of a band node is the moment of the selected parts of Omega^PML, exactly
 as the discrete collision applies them (Eq. pml-general, per time step), at the nearest fluid
 node x_f (the outermost PML layer, where sigma = sigma_max), with the sign of the collision
-term (a damping; the printed "+" of Eq. NSF-CHAR-PML would amplify); the conserved-variable
+term (a damping; the printed "+" of Eq. NSF-CHAR-PML is available as an option); the conserved-variable
 source (mass, momentum, energy = sum f |xi|^2 / 2) is mapped to the primitive variables by the
 exact chain rule at the time-n state of x_f (the printed scaling vector S is its diagonal
 part), and added to dU/dt of every layer of the band, frozen over the Runge-Kutta stages like

@@ -48,7 +48,8 @@ class OracleLBM:
         on it; Wy defaults to 0 then); the x edges keep the chosen BC. sigma_split: the
         general sigma_x != sigma_y form of Eq. (pml-general) instead of sigma_x = sigma_y.
         pml_source: bitmask of the PML source terms I (1), II (2), III (4) of Eq. NSF-CHAR-PML
-        added to the characteristic targets (Appendix; 0 = the characteristic BC of Sec. 4)."""
+        added to the characteristic targets (Appendix; 0 = the characteristic BC of Sec. 4);
+        + 8: the sign printed there instead of the collision term's."""
         self.lat = lattice(q)
         self.pml_on = pml_on
         self.periodic_y = bool(periodic_y)
@@ -241,12 +242,14 @@ class OracleLBM:
                 gx, gy = pml.gradient(Q, self.periodic_y)                    # 4
                 om = pml.omega_pml(lat.e, gx, gy, fhat, Q, self.sigma_x, self.sigma_y)
                 fstar[Fs] = fstar[Fs] + np.where(self.in_P, om, 0.0)         # 5 (PML part)
-                if self.bc == "nrbc" and self.pml_source:
+                if self.bc == "nrbc" and self.pml_source & 7:
                     parts = pml.omega_pml_terms(lat.e, gx, gy, fhat, Q, self.sigma_x,
                                                 self.sigma_y)
                     sel = sum(pt for k, pt in enumerate(parts) if self.pml_source >> k & 1)
                     M = self.M
                     Uf = np.stack([rho, u[0], u[1], T], axis=-1)[M:M + self.Ly, M:M + self.Lx]
+                    if self.pml_source & 8:                  # printed "+" of Eq. NSF-CHAR-PML
+                        sel = -sel
                     self._src = self._edge_sources(np.where(self.in_P, sel, 0.0), Uf)
             if self.periodic_y:
                 # the rows beyond a periodic y axis carry the post-collision populations of

@@ -361,7 +361,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
     return fail("periodic mode has no PML");
   if (bp.periodic_y && (W4[2] || W4[3])) return fail("a periodic y axis has no PML");
   if (bp.periodic_y && bc == LBM_BC_PERIODIC) return fail("periodic_y needs a ZG or NRBC x edge");
-  if (bp.pml_source < 0 || bp.pml_source > 7) return fail("pml_source is a bitmask of 1, 2, 4");
+  if (bp.pml_source < 0 || bp.pml_source > 15) return fail("pml_source is a bitmask of 1, 2, 4, 8");
   if (!(bp.rho0 > 0) || !(bp.T0 > 0) || !std::isfinite(bp.u0x) || !std::isfinite(bp.u0y) ||
       !std::isfinite(bp.beta))
     return fail("bad mean state or beta");

@@ -63,7 +63,8 @@ struct BcParams {
   int bc;            // 0 periodic, 1 zero gradient, 2 characteristic
   int edge[4];       // W E S N: 0 PNR-LODI, 1 CBC relax
   double beta, relax_sign, r, omega, inv_r;
-  int pml_source;    // bitmask of the Appendix PML source terms I (1), II (2), III (4)
+  int pml_source;    // bitmask of the Appendix PML source terms I (1), II (2), III (4);
+                     // 8: with the printed sign instead of the collision's
 };
 
 __host__ __device__ inline long long gindex(const Geom& g, int x, int y) {

@@ -117,7 +117,7 @@ __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
   // time-n state of the outermost fluid node: d rho = s_m, rho du = s_mom - u s_m,
   // (D/2) rho dT = s_E - u . s_mom + (u^2/2 - (D/2) T) s_m (D = 2); constant over the stages
   double src[4] = {0, 0, 0, 0};
-  if (bc.pml_source && live) {
+  if ((bc.pml_source & 7) && live) {
     const int ns = 2 * (Lx + Ly);
     const int sb = (e == 0 ? 0 : e == 1 ? Ly : e == 2 ? 2 * Ly : 2 * Ly + Lx) + wr(t);
     const int ub = ueoff + wr(t);
@@ -127,6 +127,8 @@ __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
     src[1] = (sx - ux * sm) / rho;
     src[2] = (sy - uy * sm) / rho;
     src[3] = (sE - ux * sx - uy * sy + (0.5 * (ux * ux + uy * uy) - T) * sm) / rho;
+    if (bc.pml_source & 8)   // the sign printed in Eq. (NSF-CHAR-PML)
+      for (int q = 0; q < 4; ++q) src[q] = -src[q];
   }
   double kk[4] = {0, 0, 0, 0};
   for (int s = 1; s <= 4; ++s) {

@@ -191,7 +191,7 @@ struct Ops {
       if (d.aux2) cudaStreamWaitEvent(d.aux2, d.fork, 0);
     }
     // Appendix PML source terms: only with a characteristic BC and a PML
-    const int src_mask = (d.bc.bc == 2 && has_pml(g)) ? d.bc.pml_source : 0;
+    const int src_mask = (d.bc.bc == 2 && has_pml(g)) ? (d.bc.pml_source & 7) : 0;
     mark(0, bs);
     if (STREAM && d.bc.bc == 2) launch_nrbc_stages(d, sizeof(Real) == 4, bs);
     mark(1, bs);

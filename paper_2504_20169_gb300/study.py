@@ -108,9 +108,17 @@ STEP_SIGMA = {
 
 
 def step_cases(q):
-    out = [("ZG", "zg", 0, 0.0), ("LODI", "nrbc", 0, 0.0)]
+    """(label, bc, W, sigma_max, Appendix source bitmask). The last ones are the Appendix
+    comparison (Fig. A.1 setting: LODI, W = 10, sigma_max = 0.001) with the PML source terms
+    I, II, III of Eq. (NSF-CHAR-PML) added to the LODI targets, with the sign of the collision
+    term and (suffix "+sign") with the printed sign."""
+    out = [("ZG", "zg", 0, 0.0, 0), ("LODI", "nrbc", 0, 0.0, 0)]
     for W in (10, 20, 40):
-        out += [("ZG", "zg", W, STEP_SIGMA[q]["ZG"][W]), ("LODI", "nrbc", W, STEP_SIGMA[q]["LODI"][W])]
+        out += [("ZG", "zg", W, STEP_SIGMA[q]["ZG"][W], 0),
+                ("LODI", "nrbc", W, STEP_SIGMA[q]["LODI"][W], 0)]
+    for src, name in ((1, "I"), (2, "II"), (4, "III"), (3, "I+II"), (7, "I+II+III")):
+        out.append((f"LODI+{name}", "nrbc", 10, 0.001, src))
+        out.append((f"LODI+{name} +sign", "nrbc", 10, 0.001, src + 8))
     return out
 
 
@@ -134,9 +142,9 @@ def run_density_step(q=37, Lx=200, Ly=20, steps=2000, sample=20, tau=0.8, Ma=0.0
             refs.append([t[:, pad:pad + Lx].contiguous() for t in f])
     results = []
     mean = (1.0, Ma, 0.0, 1.0)
-    for label, bc, W, sig in step_cases(q):
+    for label, bc, W, sig, src in step_cases(q):
         s = Solver(Lx, Ly, W, tau, sig, 2, bc, q, (0, 0, 0, 0), 0.0, mean,
-                   precision=precision, periodic_y=True)
+                   precision=precision, periodic_y=True, pml_source=src)
         fields = wl.density_step(Lx, Ly, Ma=Ma, W=W, Wy=0)
         s.init(*fields)
         e = {"rho": [], "ux": []}

@@ -172,7 +172,7 @@ def test_parity_split_sigma(widths, bc, precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
 @pytest.mark.parametrize("src,case", [(1, "pulse"), (7, "pulse"), (1, "step"), (2, "step"),
-                                      (5, "split")])
+                                      (9, "step"), (5, "split")])
 def test_parity_pml_aware_characteristic_bc(src, case, precision):
     """Appendix, Eq. (NSF-CHAR-PML): the moments of the selected parts of Omega^PML at the
     outermost fluid node added to the characteristic targets (terms I, II, III as a bitmask):

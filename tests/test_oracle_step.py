@@ -378,7 +378,7 @@ def test_pml_source_first_step_closed_form():
     d rho / dt = -2 sigma_max delta (the mass moment of -2 sigma f_hat), du = dT = 0; term I
     alone gives zero."""
     nx, W, s, d = 16, 6, 0.05, 1e-3
-    for src, want in ((2, -2.0 * s * d), (1, 0.0), (7, -2.0 * s * d)):
+    for src, want in ((2, -2.0 * s * d), (1, 0.0), (7, -2.0 * s * d), (10, 2.0 * s * d)):
         o = OracleLBM(nx, nx, W, 0.7, s, 2, "nrbc", pml_source=src)
         o.init(*wl.uniform(nx, nx, W, rho=1.0 + d))
         o.step(1)
