@@ -15,6 +15,13 @@ CASES = [
                 beta=0.2, mean=(1.0, 0.1, 0.0, 1.0)),
     case_kwargs(nx=96, ny=80, W=12, tau=0.8, sigma_max=0.05, bc="nrbc", nrbc_edges=(0, 1, 0, 0),
                 beta=0.3, mean=(1.0, 0.2, 0.0, 1.0)),
+    # periodic y axis, CBC relax on the x edges, Appendix PML source
+    case_kwargs(nx=60, ny=12, W=8, tau=0.8, sigma_max=0.05, sigma_power=2, bc="nrbc",
+                nrbc_edges=(1, 1, 0, 0), beta=0.2, mean=(1.0, 0.05, 0.0, 1.0), periodic_y=True,
+                pml_source=3),
+    # per-edge widths with the split sigma form
+    case_kwargs(nx=40, ny=30, W=0, tau=0.75, sigma_max=0.15, sigma_power=2, bc="zg",
+                widths=(3, 10, 0, 5), split=True),
 ]
 
 
@@ -24,7 +31,11 @@ def fields_of(k, kw):
     if k == 1:
         return wl.pressure_pulse(kw["nx"], kw["ny"], kw["W"], amp=2e-3, halfwidth=3.0,
                                  u0=(0.1, 0.0))
-    return wl.isentropic_vortex(kw["nx"], kw["ny"], kw["W"], R=8.0, mean_u=(0.2, 0.0))
+    if k == 2:
+        return wl.isentropic_vortex(kw["nx"], kw["ny"], kw["W"], R=8.0, mean_u=(0.2, 0.0))
+    if k == 3:
+        return wl.density_step(kw["nx"], kw["ny"], Ma=0.05, W=kw["W"], Wy=0)
+    return wl.random_smooth_state(kw["nx"], kw["ny"], kw["widths"], seed=4, du=0.03)
 
 
 def alone(k, steps, precision):
@@ -42,18 +53,18 @@ def test_batch_results_equal_alone_with_midrun_admission(precision):
     for k, s in enumerate(solvers):
         s.init(*fields_of(k, CASES[k]))
     b = Batch()
-    b.set(solvers[:2])                 # instance 2 arrives later
+    b.set(solvers[:2])                 # instances 2.. arrive later
     assert b.step(20)
     b.set(solvers)                     # admitted while the others are resident
     assert b.step(25)
-    b.set([solvers[0], solvers[2]])    # instance 1 retires after 45 steps
+    b.set([solvers[0]] + solvers[2:])  # instance 1 retires after 45 steps
     assert b.step(15)
     got = [s.moments() for s in solvers]
     b.close()
     for s in solvers:
         s.close()
-    steps = [60, 45, 40]
-    for k in range(3):
+    steps = [60, 45] + [40] * (len(CASES) - 2)
+    for k in range(len(CASES)):
         ref = alone(k, steps[k], precision)
         for g, r in zip(got[k], ref):
             assert np.array_equal(g, r), k
@@ -68,7 +79,7 @@ def test_unstable_member_is_retired_without_touching_others():
                                     dict(zip(("rho", "ux", "uy", "T"), kw["mean"])),
                                     nrbc_edges=kw["nrbc_edges"], beta=kw["beta"],
                                     mean=kw["mean"]), 30)
-            for k, kw in enumerate(CASES)]
+            for k, kw in enumerate(CASES[:3])]
     # poison instance 1 right after it is admitted
     orig = eng._start
 
