@@ -185,33 +185,48 @@ cudaError_t launch_nrbc_stages(const Dev& d, bool fp32, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-__global__ void k_reduce_final(const double* __restrict__ partials, int n, unsigned min_mask,
-                               double* __restrict__ out) {
-  __shared__ double sh[256];
-  for (int k = 0; k < 12; ++k) {
-    const bool is_min = (min_mask >> k) & 1u;
-    double a = is_min ? DBL_MAX : 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const double v = partials[12ll * i + k];
-      a = is_min ? fmin(a, v) : a + v;
+// Final pass of the FP64 reductions: one block of 1024 threads; each thread folds whole
+// 12-value records (contiguous, so a warp reads 32 consecutive records), then warp shuffles and
+// one shared-memory round combine the 32 warps. Sums, except the slots flagged in min_mask
+// (minimum).
+__global__ void __launch_bounds__(1024) k_reduce_final(const double* __restrict__ partials, int n,
+                                                      unsigned min_mask,
+                                                      double* __restrict__ out) {
+  __shared__ double sh[32][12];
+  double a[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) a[k] = ((min_mask >> k) & 1u) ? DBL_MAX : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double* r = partials + 12ll * i;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a[k] = ((min_mask >> k) & 1u) ? fmin(a[k], r[k]) : a[k] + r[k];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 12; ++k)
+    for (int o = 16; o > 0; o >>= 1) {
+      const double t = __shfl_down_sync(0xffffffffu, a[k], o);
+      a[k] = ((min_mask >> k) & 1u) ? fmin(a[k], t) : a[k] + t;
     }
-    sh[threadIdx.x] = a;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        const double o = sh[threadIdx.x + s];
-        sh[threadIdx.x] = is_min ? fmin(sh[threadIdx.x], o) : sh[threadIdx.x] + o;
+  if (lane == 0)
+    for (int k = 0; k < 12; ++k) sh[warp][k] = a[k];
+  __syncthreads();
+  if (warp == 0) {
+    for (int k = 0; k < 12; ++k) {
+      const bool mn = (min_mask >> k) & 1u;
+      double b = lane < nwarps ? sh[lane][k] : (mn ? DBL_MAX : 0.0);
+      for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_down_sync(0xffffffffu, b, o);
+        b = mn ? fmin(b, t) : b + t;
       }
-      __syncthreads();
+      if (lane == 0) out[k] = b;
     }
-    if (threadIdx.x == 0) out[k] = sh[0];
-    __syncthreads();
   }
 }
 
 cudaError_t reduce_partials(const double* partials, int n, unsigned min_mask, double* out,
                             cudaStream_t st) {
-  k_reduce_final<<<1, 256, 0, st>>>(partials, n, min_mask, out);
+  k_reduce_final<<<1, 1024, 0, st>>>(partials, n, min_mask, out);
   return cudaGetLastError();
 }
 
