@@ -116,7 +116,7 @@ def paper_vortex(nx, ny, W, Ma=0.1, b=0.2, rstar=0.5, K=180.0, rho0=1.0, T0=1.0,
     x* = 2(x - 1)/(nx - 1) - 1 (x counted from 1 over the bulk), centre (K/(nx - 1), 0); inside
     radius r*: u = u0 + (5/2) u0 2^(-(x^2 + y^2)/b^2) (y, -x), T = T0 + y (5/2) u0 2^(...),
     rho = rho0; u0 = Ma (c_s = 1). The paper does not give b, r*, K: b = 0.2, r* = 0.5, K = 180
-    are this build's choice. `pad` extends the grid by pad nodes per side with the same formula
+    are chosen here. `pad` extends the grid by pad nodes per side with the same formula
     (periodic reference runs), on top of the W PML layers."""
     Ly, Lx = ny + 2 * (W + pad), nx + 2 * (W + pad)
     y, x = np.meshgrid(np.arange(Ly, dtype=np.float64) - (W + pad) + 1.0,
