@@ -341,6 +341,23 @@ def main():
                 "hbm_frac": round(interior * 2 * 37 * 8 / (int64_ms * 1e-3) / 1e9 /
                                   peaks["hbm_gbs"], 4),
                 "bound": "alu (FP64 pipe)"}
+        # accuracy of the FP32 deviation storage against the FP64 path on the same solve
+        res = {}
+        for prec in ("fp32dev", "fp64"):
+            with Solver(c.nx, c.ny, c.W, c.tau, c.sigma_max, c.sigma_power, c.bc, 37,
+                        c.nrbc_edges, c.beta, c.mean, precision=prec) as s:
+                s.init(*fields)
+                s.step(args.window)
+                res[prec] = (s.moments(region="F", device=True),
+                             s.moments(region="bulk", device=True))
+        for reg, key in ((0, "fp32_vs_fp64_rel_l2"), (1, "fp32_vs_fp64_rel_l2_bulk")):
+            err = {}
+            for name, a, b in zip(("rho", "ux", "uy", "T"), res["fp32dev"][reg], res["fp64"][reg]):
+                den = torch.linalg.vector_norm(b) if name in ("rho", "T") else \
+                    torch.clamp(torch.linalg.vector_norm(b), min=math.sqrt(b.numel()))
+                err[name] = float(f"{float(torch.linalg.vector_norm(a - b) / den):.3e}")
+            fp64[key] = err
+        fp64["fp32_vs_fp64_after_steps"] = args.window
 
     # end to end through the C ABI with host buffers
     pin = [torch.from_numpy(np.ascontiguousarray(f)).pin_memory() for f in fields]
