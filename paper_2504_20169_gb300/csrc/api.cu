@@ -415,11 +415,12 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   }
   if (cudaMalloc(&ctx->V, sizeof(double) * 16 * (size_t)g.nb) != cudaSuccess) return oom("targets");
   if (cudaMalloc(&ctx->Uedge, sizeof(double) * 2 * edge_slots(g)) != cudaSuccess) return oom("edges");
-  cudaMemset(ctx->V, 0, sizeof(double) * 16 * (size_t)g.nb);
-  cudaMemset(ctx->Uedge, 0, sizeof(double) * 2 * edge_slots(g));
-  if (cudaMalloc(&ctx->Sedge, sizeof(double) * 2 * source_slots(g)) != cudaSuccess)
+  if (cudaMemset(ctx->V, 0, sizeof(double) * 16 * (size_t)g.nb) != cudaSuccess ||
+      cudaMemset(ctx->Uedge, 0, sizeof(double) * 2 * edge_slots(g)) != cudaSuccess)
+    return oom("targets");
+  if (cudaMalloc(&ctx->Sedge, sizeof(double) * 2 * source_slots(g)) != cudaSuccess ||
+      cudaMemset(ctx->Sedge, 0, sizeof(double) * 2 * source_slots(g)) != cudaSuccess)
     return oom("PML source");
-  cudaMemset(ctx->Sedge, 0, sizeof(double) * 2 * source_slots(g));
   if (cudaMalloc(&ctx->staging, fieldbytes) != cudaSuccess) return oom("staging");
   if (cudaMalloc(&ctx->partials, sizeof(double) * 12 * (size_t)ctx->max_blocks) != cudaSuccess)
     return oom("partials");
