@@ -150,6 +150,15 @@ lbm_status lbm_lattice_info(lbm_stencil stencil, int* q, int* e, double* w, doub
  * the bulk starts at (W_w, W_s) of F. */
 lbm_status lbm_geometry(const lbm_ctx* ctx, int64_t* out);
 
+/* Debugging aid (no counterpart in the paper; stands in for a memory checker). Every device
+ * buffer a context allocates sits between two 256-byte guard bands filled with 0xA5 at
+ * creation. Synchronizes the context stream and sets *intact = 1 if every guard band still
+ * holds its pattern, 0 if a kernel wrote outside a buffer. Test hook: if the environment
+ * variable LBM_DEBUG_ALLOC_BUDGET holds a byte count when lbm_create runs, allocations beyond
+ * that many payload bytes fail as if the device were out of memory (LBM_ENOMEM, nothing left
+ * allocated). */
+lbm_status lbm_debug_check_guards(lbm_ctx* ctx, int* intact);
+
 /* Debug / checkpoint: the stored post-collision populations of the last completed step (or
  * of the initial collision) on the whole grid G = (Lx + 2M) x (Ly + 2M), as float64 absolute
  * populations, layout [i][gy][gx]; host buffer of q * Gx * Gy doubles. Synchronizes. */

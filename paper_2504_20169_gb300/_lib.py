@@ -52,6 +52,7 @@ PROTOTYPES = {
     "lbm_error_sums": (C.c_int, [_ctx, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _dp]),
     "lbm_lattice_info": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp, _dp]),
     "lbm_geometry": (C.c_int, [_ctx, C.POINTER(C.c_int64)]),
+    "lbm_debug_check_guards": (C.c_int, [_ctx, C.POINTER(C.c_int)]),
     "lbm_export_populations": (C.c_int, [_ctx, _dp]),
     "lbm_import_populations": (C.c_int, [_ctx, _dp]),
     "lbm_checkpoint_size": (C.c_int, [_ctx, C.POINTER(C.c_size_t)]),

@@ -2,6 +2,7 @@
 // and the host-side sequencing of the kernels.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -197,8 +198,31 @@ struct lbm_ctx {
   bool use_graphs = true;
   std::vector<cudaEvent_t> prof;   // kKernelClasses * 2 events per recorded step
   int prof_cap = 0, prof_used = 0;
+  // device buffers: base pointer (guard band of kGuard bytes on both sides) and payload size
+  std::vector<std::pair<char*, size_t>> allocs;
+  size_t alloc_total = 0, alloc_budget = 0;  // budget 0: unlimited (test hook, see lbm.h)
   std::string err;
 };
+
+// Every device buffer of a context sits between two guard bands of kGuard bytes filled with
+// kGuardByte; lbm_debug_check_guards reports whether any kernel wrote into them.
+static const size_t kGuard = 256;
+static const int kGuardByte = 0xA5;
+
+static cudaError_t dalloc(lbm_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (ctx->alloc_budget && ctx->alloc_total + bytes > ctx->alloc_budget)
+    return cudaErrorMemoryAllocation;
+  char* base = nullptr;
+  cudaError_t e = cudaMalloc((void**)&base, bytes + 2 * kGuard);
+  if (e != cudaSuccess) return e;
+  ctx->allocs.push_back({base, bytes});
+  ctx->alloc_total += bytes;
+  if ((e = cudaMemset(base, kGuardByte, kGuard)) != cudaSuccess) return e;
+  if ((e = cudaMemset(base + kGuard + bytes, kGuardByte, kGuard)) != cudaSuccess) return e;
+  *p = base + kGuard;
+  return cudaSuccess;
+}
 
 #define LBM_CK(call)                                                          \
   do {                                                                        \
@@ -226,13 +250,8 @@ static void free_all(lbm_ctx* ctx) {
   if (ctx->join) cudaEventDestroy(ctx->join);
   if (ctx->join2) cudaEventDestroy(ctx->join2);
   if (ctx->ready) cudaEventDestroy(ctx->ready);
-  for (int k = 0; k < 2; ++k) { cudaFree(ctx->f[k]); cudaFree(ctx->S[k]); }
-  cudaFree(ctx->V);
-  cudaFree(ctx->Uedge);
-  cudaFree(ctx->Sedge);
-  cudaFree(ctx->staging);
-  cudaFree(ctx->partials);
-  cudaFree(ctx->dout);
+  for (auto& a : ctx->allocs) cudaFree(a.first);
+  ctx->allocs.clear();
   if (ctx->hout) cudaFreeHost(ctx->hout);
   if (ctx->hflag) cudaFreeHost(ctx->hflag);
 }
@@ -372,6 +391,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   if ((long long)grid->nx * grid->ny > (1ll << 31) / 2) return fail("grid too large");
 
   lbm_ctx* ctx = new lbm_ctx();
+  if (const char* b = std::getenv("LBM_DEBUG_ALLOC_BUDGET")) ctx->alloc_budget = std::strtoull(b, nullptr, 10);
   ctx->q = q;
   ctx->prec = precision;
   ctx->bc = bc;
@@ -406,25 +426,28 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
     return LBM_ENOMEM;
   };
   for (int k = 0; k < 2; ++k) {
-    if (cudaMalloc(&ctx->f[k], ctx->fbytes) != cudaSuccess) return oom("populations");
+    if (dalloc(ctx, &ctx->f[k], ctx->fbytes) != cudaSuccess) return oom("populations");
     if (cudaMemset(ctx->f[k], 0, ctx->fbytes) != cudaSuccess) return oom("populations");
     if (has_pml(g)) {
-      if (cudaMalloc(&ctx->S[k], ctx->sbytes) != cudaSuccess) return oom("PML accumulator");
+      if (dalloc(ctx, &ctx->S[k], ctx->sbytes) != cudaSuccess) return oom("PML accumulator");
       if (cudaMemset(ctx->S[k], 0, ctx->sbytes) != cudaSuccess) return oom("PML accumulator");
     }
   }
-  if (cudaMalloc(&ctx->V, sizeof(double) * 16 * (size_t)g.nb) != cudaSuccess) return oom("targets");
-  if (cudaMalloc(&ctx->Uedge, sizeof(double) * 2 * edge_slots(g)) != cudaSuccess) return oom("edges");
+  if (dalloc(ctx, (void**)&ctx->V, sizeof(double) * 16 * (size_t)g.nb) != cudaSuccess)
+    return oom("targets");
+  if (dalloc(ctx, (void**)&ctx->Uedge, sizeof(double) * 2 * edge_slots(g)) != cudaSuccess)
+    return oom("edges");
   if (cudaMemset(ctx->V, 0, sizeof(double) * 16 * (size_t)g.nb) != cudaSuccess ||
       cudaMemset(ctx->Uedge, 0, sizeof(double) * 2 * edge_slots(g)) != cudaSuccess)
     return oom("targets");
-  if (cudaMalloc(&ctx->Sedge, sizeof(double) * 2 * source_slots(g)) != cudaSuccess ||
+  if (dalloc(ctx, (void**)&ctx->Sedge, sizeof(double) * 2 * source_slots(g)) != cudaSuccess ||
       cudaMemset(ctx->Sedge, 0, sizeof(double) * 2 * source_slots(g)) != cudaSuccess)
     return oom("PML source");
-  if (cudaMalloc(&ctx->staging, fieldbytes) != cudaSuccess) return oom("staging");
-  if (cudaMalloc(&ctx->partials, sizeof(double) * 12 * (size_t)ctx->max_blocks) != cudaSuccess)
+  if (dalloc(ctx, (void**)&ctx->staging, fieldbytes) != cudaSuccess) return oom("staging");
+  if (dalloc(ctx, (void**)&ctx->partials, sizeof(double) * 12 * (size_t)ctx->max_blocks) !=
+      cudaSuccess)
     return oom("partials");
-  if (cudaMalloc(&ctx->dout, sizeof(double) * 16) != cudaSuccess) return oom("outputs");
+  if (dalloc(ctx, (void**)&ctx->dout, sizeof(double) * 16) != cudaSuccess) return oom("outputs");
   if (cudaHostAlloc(&ctx->hout, sizeof(double) * 16, cudaHostAllocDefault) != cudaSuccess)
     return oom("pinned outputs");
   if (cudaHostAlloc(&ctx->hflag, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
@@ -497,6 +520,22 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
 
 const char* lbm_last_error(const lbm_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+lbm_status lbm_debug_check_guards(lbm_ctx* ctx, int* intact) {
+  if (!ctx || !intact) return LBM_EINVAL;
+  LBM_CK(cudaSetDevice(ctx->device));
+  LBM_CK(cudaStreamSynchronize(ctx->st));
+  *intact = 1;
+  std::vector<unsigned char> h(kGuard);
+  for (const auto& a : ctx->allocs)
+    for (int side = 0; side < 2; ++side) {
+      LBM_CK(cudaMemcpy(h.data(), a.first + (side ? kGuard + a.second : 0), kGuard,
+                        cudaMemcpyDeviceToHost));
+      for (unsigned char v : h)
+        if (v != (unsigned char)kGuardByte) *intact = 0;
+    }
+  return LBM_OK;
 }
 
 lbm_status lbm_geometry(const lbm_ctx* ctx, int64_t* out) {

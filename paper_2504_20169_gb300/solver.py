@@ -180,6 +180,12 @@ class Solver:
         _check(L.lib().lbm_profile_read(self.ctx, ms, C.byref(n)), self.ctx)
         return dict(zip(self.KERNEL_CLASSES, ms[:])), n.value
 
+    def guards_intact(self):
+        """True if no kernel wrote outside the context's device buffers (guard bands)."""
+        v = C.c_int()
+        _check(L.lib().lbm_debug_check_guards(self.ctx, C.byref(v)), self.ctx)
+        return bool(v.value)
+
     @property
     def steps(self):
         g = (C.c_int64 * 12)()
