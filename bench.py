@@ -250,7 +250,7 @@ def serving_runs(args):
     eng = Engine(budget_bytes=100e9, precision="fp32dev", chunk=150, keep_fields=False)
     eng.run(reqs)
     eng.close()
-    b = summarize(reqs, eng.wall, eng.sites_steps)
+    b = summarize(reqs, eng.wall, eng.sites_steps, eng.step_seconds)
     b["what"] = "32 instances of the seeded batched sweep (N 128..1024, W 4..64, ZG/NRBC, " \
                 "pulse/vortex), 150 steps each, one combined graph per step; wall clock " \
                 "includes admission (host IC + upload) and retirement"
@@ -259,7 +259,7 @@ def serving_runs(args):
     eng = Engine(budget_bytes=40e9, precision="fp32dev", chunk=50, keep_fields=False)
     eng.run(reqs)
     eng.close()
-    sv = summarize(reqs, eng.wall, eng.sites_steps)
+    sv = summarize(reqs, eng.wall, eng.sites_steps, eng.step_seconds)
     sv["what"] = "Poisson stream 50/s, 48 requests, bulk log-uniform 64..1024, PML 8..64, " \
                  "100..300 steps, 40 GB admission budget, chunks of 50 steps; latency from " \
                  "arrival to fields on the host"

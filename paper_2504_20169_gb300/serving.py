@@ -114,6 +114,7 @@ class Engine:
         self.batch = Batch()
         self.steps_done = 0
         self.sites_steps = 0
+        self.step_seconds = 0.0   # wall time of the batched stepping alone (launch to sync)
 
     def _start(self, r, now):
         c = r.case
@@ -156,6 +157,7 @@ class Engine:
                 continue
             n = min(self.chunk, min(r.remaining for r in running))
             self.batch.set([r.solver for r in running])
+            t_step = clock()
             if not self.batch.step(n):
                 for r in list(running):
                     try:
@@ -165,6 +167,7 @@ class Engine:
                         self._finish(r, clock() - t0, status="unstable")
                 continue
             torch.cuda.current_stream().synchronize()
+            self.step_seconds += clock() - t_step
             for r in running:
                 r.remaining -= n
                 self.sites_steps += (r.case.nx + 2 * r.case.W) * (r.case.ny + 2 * r.case.W) * n
@@ -179,12 +182,15 @@ class Engine:
         self.batch.close()
 
 
-def summarize(requests, wall, sites_steps):
+def summarize(requests, wall, sites_steps, step_seconds=None):
     lat = np.array([r.latency for r in requests if r.status == "done"])
     out = {"requests": len(requests), "done": int(np.sum([r.status == "done" for r in requests])),
            "unstable": int(np.sum([r.status == "unstable" for r in requests])),
            "rejected": int(np.sum([r.status == "rejected" for r in requests])),
            "wall_s": wall, "aggregate_mlups": sites_steps / wall / 1e6 if wall > 0 else 0.0}
+    if step_seconds:
+        out["stepping_s"] = step_seconds
+        out["stepping_mlups"] = sites_steps / step_seconds / 1e6
     if lat.size:
         out["latency_p50_s"] = float(np.percentile(lat, 50))
         out["latency_p99_s"] = float(np.percentile(lat, 99))
@@ -215,7 +221,7 @@ def main():
     reqs = [Request(k, t, c, c.steps) for k, (t, c) in enumerate(stream)]
     eng = Engine(a.budget_gb * 1e9, a.precision, a.chunk, keep_fields=False)
     eng.run(reqs)
-    out = summarize(reqs, eng.wall, eng.sites_steps)
+    out = summarize(reqs, eng.wall, eng.sites_steps, eng.step_seconds)
     out.update({"rate_per_s": a.rate, "steps": [a.smin, a.smax], "nmax": a.nmax,
                 "precision": a.precision, "budget_gb": a.budget_gb})
     print(json.dumps(out))
