@@ -229,11 +229,29 @@ def test_totals_and_error_sums_match_oracle():
         assert sums[3 * k + 1] == pytest.approx(np.sum(r * r), rel=1e-13)
 
 
+CKPT_CASES = {
+    "square": (case_kwargs(nx=40, ny=36, W=6, tau=0.7, sigma_max=0.1, bc="nrbc",
+                           nrbc_edges=(1, 0, 0, 1), beta=0.3, mean=(1.0, 0.1, 0.0, 1.0)),
+               lambda: wl.isentropic_vortex(40, 36, 6, R=6.0, mean_u=(0.1, 0.0))),
+    # periodic y, CBC relax on the x edges, Appendix source (edge moments and sources restored)
+    "periodic_src": (case_kwargs(nx=60, ny=12, W=8, tau=0.8, sigma_max=0.05, sigma_power=2,
+                                 bc="nrbc", nrbc_edges=(1, 1, 0, 0), beta=0.2,
+                                 mean=(1.0, 0.05, 0.0, 1.0), periodic_y=True, pml_source=7),
+                     lambda: wl.density_step(60, 12, Ma=0.05, W=8, Wy=0)),
+    # per-edge widths, split sigma
+    "per_edge": (case_kwargs(nx=38, ny=30, W=0, tau=0.75, sigma_max=0.15, sigma_power=2,
+                             bc="nrbc", widths=(4, 9, 3, 6), split=True, pml_source=1,
+                             mean=(1.0, 0.04, 0.0, 1.0)),
+                 lambda: wl.random_smooth_state(38, 30, (4, 9, 3, 6), seed=5, du=0.03,
+                                                mean_u=(0.04, 0.0))),
+}
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
-def test_checkpoint_restore_continues_bit_identically(precision):
-    kw = case_kwargs(nx=40, ny=36, W=6, tau=0.7, sigma_max=0.1, bc="nrbc",
-                     nrbc_edges=(1, 0, 0, 1), beta=0.3, mean=(1.0, 0.1, 0.0, 1.0))
-    fields = wl.isentropic_vortex(40, 36, 6, R=6.0, mean_u=(0.1, 0.0))
+@pytest.mark.parametrize("case", sorted(CKPT_CASES))
+def test_checkpoint_restore_continues_bit_identically(case, precision):
+    kw, make_fields = CKPT_CASES[case]
+    fields = make_fields()
     with make_solver(kw, precision) as a, make_solver(kw, precision) as b:
         a.init(*fields)
         a.step(10)
