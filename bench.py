@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--window", type=int, default=200,
                     help="steps per fresh solve; the printed PML stays finite on this workload "
                          "for about 300 steps (tau 0.55), so timed steps run in windows")
+    ap.add_argument("--variants", type=int, default=1,
+                    help="also time the other stencils and PML / boundary variants (1) or not (0)")
     ap.add_argument("--serving", type=int, default=1,
                     help="also run the batched sweep and the serving stream (0 skips)")
     ap.add_argument("--size", type=int, default=2048,
@@ -239,6 +241,54 @@ def timed_run(Solver, c, fields, precision, steps, warmup, dev, window, prof_ste
     return total, per, prof, ck, tot
 
 
+def variant_runs(size, window, warmup):
+    """Step time of the other built variants on the same 2048^2-class grid (FP32 deviation
+    storage, one CUDA-graph replay per step, events per step): the D2Q17 / D2Q9 stencils, an
+    outlet-heavy per-edge PML (W 8 / 32 / 8 / 8), the split sigma_x != sigma_y form, the
+    Appendix PML source (terms I + II + III) and a periodic y axis with open x edges."""
+    import torch
+    import workloads as wl
+    from paper_2504_20169_gb300 import Solver
+    c = wl.vortex_2048(n=size)
+    base = dict(sigma_max=c.sigma_max, sigma_power=c.sigma_power, bc=c.bc, q=37,
+                nrbc_edges=c.nrbc_edges, beta=c.beta, mean=c.mean)
+    runs = {
+        "D2Q17": dict(base, q=17),
+        "D2Q9": dict(base, q=9),
+        "per_edge_8_32_8_8": dict(base, pml_widths=(8, 32, 8, 8)),
+        "split_sigma": dict(base, sigma_split=True),
+        "pml_source_I_II_III": dict(base, pml_source=7),
+        "periodic_y_W32_x": dict(base, periodic_y=True, nrbc_edges=(0, 1, 0, 0)),
+    }
+    out = {}
+    for name, kw in runs.items():
+        W = c.W
+        widths = kw.get("pml_widths")
+        py = kw.get("periodic_y", False)
+        fw = widths if widths is not None else (W, W, 0, 0) if py else W
+        fields = wl.isentropic_vortex(size, size, fw, R=20.0, Mv=0.05, mean_u=(0.3, 0.0))
+        s = Solver(size, size, W, c.tau, kw["sigma_max"], kw["sigma_power"], kw["bc"], kw["q"],
+                   kw["nrbc_edges"], kw["beta"], kw["mean"], precision="fp32dev",
+                   pml_widths=widths, periodic_y=py, sigma_split=kw.get("sigma_split", False),
+                   pml_source=kw.get("pml_source", 0))
+        s.init(*fields)
+        s.step(warmup)
+        s.init(*fields)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(st)
+        s.step(window)
+        ev[1].record(st)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / window
+        nodes = s.Lx * s.Ly
+        out[name] = {"ms_per_step": round(ms, 4), "mlups": round(nodes / (ms * 1e-3) / 1e6, 1),
+                     "nodes": nodes, "finite": bool(s.reduce()[6] == 0)}
+        s.close()
+    return out
+
+
 def serving_runs(args):
     """Batched sweep (32 seeded uneven instances, all admitted at t = 0, 150 steps each) and a
     seeded Poisson request stream (48 requests at 50/s, bulk 64..1024, 100..300 steps), both in
@@ -389,6 +439,7 @@ def main():
     batched = serving = None
     if args.serving:
         batched, serving = serving_runs(args)
+    variants = variant_runs(args.size, args.window, args.warmup) if args.variants else None
 
     if rank == 0:
         cpu = oracle_sample(args.cpu_seconds) if args.cpu_seconds > 0 else None
@@ -410,6 +461,7 @@ def main():
             "latency_ms": {"p50": round(statistics.median(per), 5),
                            "p99": round(per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)], 5)},
             "roofline": roof, "step_roofline": step_roof, "fp64": fp64, "batched_fp32": batched, "serving": serving,
+            "variants_fp32": variants,
             "e2e": e2e, "cpu_baseline": cpu,
             # per step: k_nrbc_rk4, k_pml_fused, k_gamma, k_bulk (one CUDA-graph replay)
             "gpu_launches": args.steps * (4 if c.bc == "nrbc" else 3), "clocks": ck,
