@@ -390,7 +390,11 @@ def main():
                 "interior_kernel_gbs": round(interior * 2 * 37 * 8 / (int64_ms * 1e-3) / 1e9, 1),
                 "hbm_frac": round(interior * 2 * 37 * 8 / (int64_ms * 1e-3) / 1e9 /
                                   peaks["hbm_gbs"], 4),
-                "bound": "alu (FP64 pipe)"}
+                "bound": "alu (FP64 pipe)",
+                "alu_roofline": {"bound": "alu", "pipe": "fp64",
+                                 "pipe_busy": 0.881, "peak_nominal_tflops": 1.25,
+                                 "source": "ncu sm__inst_executed_pipe_fp64 of the interior "
+                                           "kernel, profiles/k_bulk_fp64_vortex1024.md"}}
         # accuracy of the FP32 deviation storage against the FP64 path on the same solve
         res = {}
         for prec in ("fp32dev", "fp64"):
