@@ -123,7 +123,7 @@ def step_cases(q):
 
 
 def run_density_step(q=37, Lx=200, Ly=20, steps=2000, sample=20, tau=0.8, Ma=0.05,
-                     precision="fp64", prof_steps=100):
+                     precision="fp64", prof_steps=100, cases=None):
     import torch
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import workloads as wl
@@ -142,7 +142,7 @@ def run_density_step(q=37, Lx=200, Ly=20, steps=2000, sample=20, tau=0.8, Ma=0.0
             refs.append([t[:, pad:pad + Lx].contiguous() for t in f])
     results = []
     mean = (1.0, Ma, 0.0, 1.0)
-    for label, bc, W, sig, src in step_cases(q):
+    for label, bc, W, sig, src in (cases if cases is not None else step_cases(q)):
         s = Solver(Lx, Ly, W, tau, sig, 2, bc, q, (0, 0, 0, 0), 0.0, mean,
                    precision=precision, periodic_y=True, pml_source=src)
         fields = wl.density_step(Lx, Ly, Ma=Ma, W=W, Wy=0)
@@ -187,10 +187,26 @@ def _fmt(v):
 def main():
     import argparse
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="all", choices=("vortex", "step", "all"))
+    ap.add_argument("--case", default="all", choices=("vortex", "step", "scan", "all"))
     ap.add_argument("--tau", type=float, default=0.8)
     ap.add_argument("--steps", type=int, default=None)
     a = ap.parse_args()
+    if a.case in ("scan", "all"):
+        # Figs. 3-4: the sigma_max scan of the density step with ZG beyond a W = 20 PML (and
+        # PNR-LODI for comparison); the first row of each block is ZG without PML (C_Z = 1)
+        print("| q | BC | W | sigma_max | e_bar rho | e_bar u_x | max e rho | C_rho | C_ux | status |")
+        print("|---|---|---|---|---|---|---|---|---|---|")
+        sig = (0.01, 0.03, 0.06, 0.10, 0.14, 0.2, 0.3, 0.6)
+        for q in (9, 17, 37):
+            cases = [("ZG", "zg", 0, 0.0, 0)] + [("ZG", "zg", 20, v, 0) for v in sig] + \
+                    [("LODI", "nrbc", 20, v, 0) for v in sig]
+            meta, results = run_density_step(q=q, steps=a.steps or 2000, tau=a.tau, cases=cases)
+            print(json.dumps(meta))
+            for r in results:
+                eb, cz = r["ebar"], r["C_Z"]
+                print(f"| {q} | {r['bc']} | {r['W']} | {r['sigma_max']} | {_fmt(eb['rho'])} | "
+                      f"{_fmt(eb['ux'])} | {_fmt(r['emax']['rho'])} | {_fmt(cz['rho'])} | "
+                      f"{_fmt(cz['ux'])} | {r['status']} |")
     if a.case in ("step", "all"):
         print("| q | BC | W | sigma_max | e_bar rho | e_bar u_x | max e rho | C_rho | C_ux | C_t |")
         print("|---|---|---|---|---|---|---|---|---|---|")
