@@ -7,10 +7,12 @@
  *     with the fourth-order mixed temperature term read as (c^2 - 6) (the printed (c^2 - 4)
  *     does not return the density it was built from);
  *   - PML: Eqs. (decomp-NJ), (PMLCOLL), (PML_ramp), (PMLQ) with the trapezoidal rule, gradients
- *     Eqs. (FD-dx-center) / (FD-dx-bw);
+ *     Eqs. (FD-dx-center) / (FD-dx-bw); optionally the general sigma_x != sigma_y form of
+ *     Eq. (pml-general) and per-edge widths (closing remark of Sec. 5);
  *   - outer boundary: zero gradient, Eq. (zg-bc), or the characteristic BC of Sec. 4
  *     (Eqs. NSF-CHAR, PNR, thermal_LODI_macro_evo, thermal_CBC_macro_evo, CBC-Relax) with
- *     non-equilibrium extrapolation.
+ *     non-equilibrium extrapolation, optionally with the PML source terms of the Appendix
+ *     (Eq. NSF-CHAR-PML); a periodic y axis for the Sec. 5.1 setting.
  *
  * Geometry. Bulk nx x ny nodes; W PML layers on every side give the fluid region F of
  * Lx x Ly = (nx + 2W) x (ny + 2W) nodes (Fig. 2) (with per-edge widths, see lbm_bc_params:
@@ -99,10 +101,11 @@ typedef struct {
 
 /* Create a context. tau > 1/2 (tau = +INFINITY gives collisionless free streaming);
  * pml_width 0 or 2..4096 (the one-sided gradient reaches two nodes inward); bc_params may be
- * NULL for the rest state (1, 0, 0, 1), PNR_LODI on every edge and pml_width on every edge. cuda_stream is a cudaStream_t
- * (NULL = the legacy default stream). Allocates the populations (2 x q x |grid| values of the
- * precision), the PML accumulator on the PML and its inner ring, and the boundary targets. On
- * failure *out is NULL and nothing stays allocated. */
+ * NULL for the rest state (1, 0, 0, 1), PNR_LODI on every edge and pml_width on every edge.
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream). Allocates the populations
+ * (2 x q x |grid| values of the precision), the PML accumulator on the PML and its inner
+ * ring, the boundary targets and the edge moments / sources (lbm_estimate_bytes gives the
+ * total). On failure *out is NULL and nothing stays allocated. */
 lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int pml_width,
                       const lbm_sigma_profile* sigma, lbm_bc_kind bc, const lbm_bc_params* bc_params,
                       lbm_precision precision, void* cuda_stream, lbm_ctx** out);
