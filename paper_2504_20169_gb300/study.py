@@ -180,6 +180,56 @@ def run_density_step(q=37, Lx=200, Ly=20, steps=2000, sample=20, tau=0.8, Ma=0.0
     return meta, results
 
 
+def run_bench_workload(steps=200, sample=20, precision="fp32dev", n=2048, W=32):
+    """e_Z of the benchmark workload itself (2048^2 + PML 32 cubic 0.1, characteristic BC with
+    CBC relax on the east edge, D2Q37, tau 0.55, isentropic vortex in a Mach 0.3 flow) against a
+    periodic reference on a grid padded by the distance the fastest signal covers; also ZG
+    without PML, ZG with the same PML and the characteristic BC without PML, for C_Z. The
+    window stays below the step count at which the PML modes of the printed scheme grow."""
+    import torch
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import workloads as wl
+    from . import Solver, lattice_info
+    _, _, r = lattice_info(37)
+    pad = int((math.sqrt(2.0) + 0.35) / r * steps * 1.05) + 8
+    tau, vort = 0.55, dict(R=20.0, Mv=0.05, mean_u=(0.3, 0.0))
+    refs = []
+    with Solver(n + 2 * pad, n + 2 * pad, 0, tau, bc="periodic", q=37, precision=precision) as ref:
+        ref.init(*wl.isentropic_vortex(n + 2 * pad, n + 2 * pad, 0, **vort))
+        for k in range(steps // sample):
+            ref.step(sample)
+            f = ref.moments(region="F", device=True)
+            refs.append([t[pad:pad + n, pad:pad + n].contiguous() for t in f])
+    mean = (1.0, 0.3, 0.0, 1.0)
+    cases = [("ZG", "zg", 0, (0, 0, 0, 0)), ("ZG + PML", "zg", W, (0, 0, 0, 0)),
+             ("CBC(A)", "nrbc", 0, (0, 1, 0, 0)), ("CBC(A) + PML (benchmark)", "nrbc", W, (0, 1, 0, 0))]
+    results = []
+    for label, bc, w, edges in cases:
+        with Solver(n, n, w, tau, 0.1 if w else 0.0, 3, bc, 37, edges, 0.3, mean,
+                    precision=precision) as s:
+            s.init(*wl.isentropic_vortex(n, n, w, **vort))
+            e = {"rho": [], "ux": [], "T": []}
+            status = "ok"
+            try:
+                for k in range(steps // sample):
+                    s.step(sample)
+                    sums = s.error_sums(refs[k])
+                    e["rho"].append(math.sqrt(sums[2]))
+                    e["ux"].append(math.sqrt(sums[5]))
+                    e["T"].append(math.sqrt(sums[11]))
+            except Exception as ex:
+                status = str(ex).split(":")[0]
+        results.append({"bc": label, "W": w, "status": status,
+                        "ebar": {k: (sum(v) / len(v) if v else None) for k, v in e.items()},
+                        "e_last": {k: (v[-1] if v else None) for k, v in e.items()}})
+    for r_ in results:
+        r_["C_Z"] = {k: (r_["ebar"][k] / results[0]["ebar"][k]
+                         if r_["ebar"][k] and results[0]["ebar"][k] else None) for k in r_["ebar"]}
+    meta = {"case": "bench_workload", "n": n, "W": W, "steps": steps, "sample": sample,
+            "precision": precision, "reference_grid": n + 2 * pad}
+    return meta, results
+
+
 def _fmt(v):
     return "n/a" if v is None else f"{v:.3g}"
 
@@ -187,10 +237,22 @@ def _fmt(v):
 def main():
     import argparse
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="all", choices=("vortex", "step", "scan", "all"))
+    ap.add_argument("--case", default="all", choices=("vortex", "step", "scan", "bench", "all"))
     ap.add_argument("--tau", type=float, default=0.8)
     ap.add_argument("--steps", type=int, default=None)
     a = ap.parse_args()
+    if a.case in ("bench", "all"):
+        # e_Z is a sum over the 2048^2 bulk (no 1/N); the rms relative error is e_Z / 2048
+        print("| precision | BC | W | e_bar rho | e_bar u_x | e_bar T | rms rel. error rho at end |")
+        print("|---|---|---|---|---|---|---|")
+        for prec in ("fp32dev", "fp64"):
+            meta, results = run_bench_workload(steps=a.steps or 200, precision=prec)
+            print(json.dumps(meta))
+            for r in results:
+                eb = r["ebar"]
+                rms = None if r["e_last"]["rho"] is None else r["e_last"]["rho"] / meta["n"]
+                print(f"| {prec} | {r['bc']} | {r['W']} | {_fmt(eb['rho'])} | {_fmt(eb['ux'])} | "
+                      f"{_fmt(eb['T'])} | {_fmt(rms)} |" + ("" if r["status"] == "ok" else f" {r['status']}"))
     if a.case in ("scan", "all"):
         # Figs. 3-4: the sigma_max scan of the density step with ZG beyond a W = 20 PML (and
         # PNR-LODI for comparison); the first row of each block is ZG without PML (C_Z = 1)
