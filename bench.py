@@ -242,8 +242,9 @@ def timed_run(Solver, c, fields, precision, steps, warmup, dev, window, prof_ste
 
 
 def variant_runs(size, window, warmup):
-    """Step time of the other built variants on the same 2048^2-class grid (FP32 deviation
-    storage, one CUDA-graph replay per step, events per step): the D2Q17 / D2Q9 stencils, an
+    """Step time of the largest single-GPU case (8192^2 + PML 64) and of the other built
+    variants on the 2048^2-class grid (FP32 deviation storage, one CUDA-graph replay per step,
+    CUDA events around the window): the D2Q17 / D2Q9 stencils, an
     outlet-heavy per-edge PML (W 8 / 32 / 8 / 8), the split sigma_x != sigma_y form, the
     Appendix PML source (terms I + II + III) and a periodic y axis with open x edges."""
     import torch
@@ -261,6 +262,29 @@ def variant_runs(size, window, warmup):
         "periodic_y_W32_x": dict(base, periodic_y=True, nrbc_edges=(0, 1, 0, 0)),
     }
     out = {}
+    # the largest single-GPU case: 8192^2 + PML 64 (about 20 GB of FP32 populations)
+    cs = wl.stress_8192()
+    with Solver(cs.nx, cs.ny, cs.W, cs.tau, cs.sigma_max, cs.sigma_power, cs.bc, 37,
+                cs.nrbc_edges, cs.beta, cs.mean, precision="fp32dev") as s:
+        fields = cs.fields()
+        s.init(*fields)
+        s.step(warmup)
+        s.init(*fields)
+        del fields
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        nst = 50
+        ev[0].record(torch.cuda.current_stream())
+        s.step(nst)
+        ev[1].record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / nst
+        nodes = s.Lx * s.Ly
+        out["stress8192_w64"] = {"ms_per_step": round(ms, 4),
+                                 "mlups": round(nodes / (ms * 1e-3) / 1e6, 1), "nodes": nodes,
+                                 "finite": bool(s.reduce()[6] == 0),
+                                 "step_hbm_frac": round(nodes * 296 / (ms * 1e-3) / 1e9 /
+                                                        measured_peaks()[0]["hbm_gbs"], 4)}
     for name, kw in runs.items():
         W = c.W
         widths = kw.get("pml_widths")
