@@ -464,10 +464,12 @@ def main():
            "what": f"{nrep} solves through the C ABI: lbm_init from pinned host fields, "
                    f"{args.window} steps, lbm_moments to pinned host; wall clock"}
 
-    batched = serving = None
-    if args.serving:
+    # informational sections (single-GPU measurements): rank 0 only, after the timed work
+    batched = serving = variants = None
+    if rank == 0 and args.serving:
         batched, serving = serving_runs(args)
-    variants = variant_runs(args.size, args.window, args.warmup) if args.variants else None
+    if rank == 0 and args.variants:
+        variants = variant_runs(args.size, args.window, args.warmup)
 
     if rank == 0:
         cpu = oracle_sample(args.cpu_seconds) if args.cpu_seconds > 0 else None
