@@ -330,7 +330,8 @@ static size_t bytes_of(const Geom& g, int q, int es) {
   return 2 * (size_t)q * g.plane * es + 2 * (size_t)q * g.Sp * es +
          sizeof(double) * (16 * (size_t)g.nb + 2 * edge_slots(g) + 2 * source_slots(g) +
                            4 * (size_t)g.Lx * g.Ly +
-                           12 * max_blocks + 16);
+                           12 * max_blocks + 16) +
+         10 * 2 * kGuard;   // guard bands of the (at most ten) device buffers
 }
 
 extern "C" lbm_status lbm_estimate_bytes(const lbm_grid* grid, lbm_stencil stencil, int pml_width,
