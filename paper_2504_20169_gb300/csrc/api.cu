@@ -312,7 +312,9 @@ static Geom make_geom(int nx, int ny, const int W[4], int M, int py) {
   g.cF0 = 32;
   g.pitch = ((g.cF0 + g.Lx + g.M) + 31) / 32 * 32;
   g.plane = ((long long)g.pitch * (g.Ly + 2 * g.M) + 63) / 64 * 64;
-  auto depth = [&](int w) { return w > 0 ? std::max(w + 1, g.M) : g.M; };
+  // the frame holds the PML and its inner ring, and at least the two outer layers whose
+  // moments the characteristic targets read (so also for D2Q9, M = 1)
+  auto depth = [&](int w) { return std::max(w > 0 ? w + 1 : 0, std::max(g.M, 2)); };
   g.Fw = depth(g.Ww);
   g.Fe = depth(g.We);
   g.Fs = py ? 0 : depth(g.Ws);

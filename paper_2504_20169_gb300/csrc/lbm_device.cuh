@@ -37,7 +37,8 @@ struct Geom {
   int pitch;         // storage row length (elements), multiple of 32
   int cF0;           // storage column of x = 0 of F, multiple of 32
   long long plane;   // elements per direction plane (pitch * (Ly + 2M))
-  int Fw, Fe, Fs, Fn; // frame depth per edge: max(W_edge + 1, M) with a PML there, else M;
+  int Fw, Fe, Fs, Fn; // frame depth per edge: max(W_edge + 1, M, 2) with a PML there, else
+                     // max(M, 2) (the two outer layers feed the characteristic targets);
                      // Fs = Fn = 0 on a periodic y axis
   int frame_n;       // number of frame nodes
   long long Sp;      // PML accumulator stride per direction

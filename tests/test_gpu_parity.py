@@ -81,13 +81,14 @@ def test_parity_vortex_nrbc_pml(precision):
     check(kw, fields, 60, precision)
 
 
+@pytest.mark.parametrize("q", [37, 17, 9])
 @pytest.mark.parametrize("edges,steps", [((1, 1, 1, 1), 40), ((0, 0, 0, 0), 80)])
-def test_parity_nrbc_without_pml(edges, steps):
+def test_parity_nrbc_without_pml(edges, steps, q):
     """Characteristic BC with no PML. With CBC relax on all four edges the case is sensitive:
     the oracle rerun from 1-ulp-perturbed inputs moves by 1.2e-12 (rho) after 80 steps, so the
     1e-12 bound is checked at 40 steps."""
     kw = case_kwargs(nx=40, ny=40, W=0, tau=0.7, sigma_max=0.0, bc="nrbc", nrbc_edges=edges,
-                     beta=0.2, mean=(1.0, 0.1, -0.05, 1.0))
+                     beta=0.2, mean=(1.0, 0.1, -0.05, 1.0), q=q)
     fields = wl.pressure_pulse(40, 40, 0, amp=2e-3, halfwidth=4.0, u0=(0.1, -0.05))
     check(kw, fields, steps)
 
@@ -205,6 +206,29 @@ def test_parity_other_stencils(q, bc, precision):
                      nrbc_edges=(0, 1, 0, 1), beta=0.2, mean=(1.0, 0.05, 0.0, 1.0))
     fields = wl.pressure_pulse(36, 30, 4, amp=1e-3, halfwidth=3.0, u0=(0.05, 0.0))
     check(kw, fields, 50, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+@pytest.mark.parametrize("q", [17, 9])
+@pytest.mark.parametrize("variant", ["per_edge_split_src", "periodic_y"])
+def test_parity_other_stencils_new_features(q, variant, precision):
+    """D2Q17 / D2Q9 (boundary depth M = 3 / 1) with per-edge widths (one edge without PML, so a
+    frame band of depth M), the split sigma form and the Appendix source, and on a periodic y
+    axis (row images M deep)."""
+    if variant == "per_edge_split_src":
+        widths = (0, 6, 3, 4)
+        kw = case_kwargs(nx=34, ny=28, W=0, tau=0.75, sigma_max=0.1, sigma_power=2, bc="nrbc",
+                         q=q, nrbc_edges=(0, 1, 0, 0), beta=0.2, mean=(1.0, 0.04, 0.0, 1.0),
+                         widths=widths, split=True, pml_source=3)
+        fields = wl.random_smooth_state(34, 28, widths, seed=q, du=0.02, mean_u=(0.04, 0.0))
+    else:
+        kw = case_kwargs(nx=40, ny=10, W=5, tau=0.75, sigma_max=0.05, sigma_power=2, bc="nrbc",
+                         q=q, nrbc_edges=(1, 1, 0, 0), beta=0.2, mean=(1.0, 0.04, 0.0, 1.0),
+                         periodic_y=True)
+        rho, ux, uy, T = wl.density_step(40, 10, Ma=0.04, W=5, Wy=0)
+        pr, pux, puy, pT = wl.random_smooth_state(40, 10, 5, seed=q + 1, du=0.01, Wy=0)
+        fields = (rho + pr - 1.0, ux + pux, uy + puy, T + pT - 1.0)
+    check(kw, fields, 30, precision)
 
 
 def test_totals_and_error_sums_match_oracle():
