@@ -26,6 +26,17 @@ Gradient: Eq. (FD-dx-center) everywhere except along an axis whose outward neigh
 outside F (outermost layer), where Eq. (FD-dx-bw) is used along the outward normal n:
 dQ/dn = (3 Q(x) - 4 Q(x - n) + Q(x - 2n)) / 2, dQ/dx_a = n_a dQ/dn.
 
+Link-integrated gradient (an option, not the printed scheme). The printed per-axis central
+differences make the scheme linearly unstable for every sigma > 0 (von Neumann analysis in the
+tests): the lattice streams each population exactly along its link while grad Q is taken by
+differences that do not follow the link, so at wavenumbers where the two disagree (e.g.
+k = 2 pi / 3 for the speed-3 populations of D2Q37, which alias to zero phase) the identity
+that makes the continuous PML stable is lost. The option pml_grad = "link" replaces
+c_i . grad Q_i by its exact integral along the path the population travels in one step,
+Q_i(x + e_i) - Q_i(x); for a field linear in x this equals the printed form. Q is then needed up to
+M nodes away from P (inside the bulk and in the boundary band Gamma), and is integrated there by
+the same trapezoidal rule from the moments of those nodes.
+
 Collision term, Eq. (pml-general):
 Omega^PML_i = -(sigma_y c_ix dQ_i/dx + sigma_x c_iy dQ_i/dy + (sigma_x + sigma_y) f_hat_i
                + sigma_x sigma_y Q_i),
@@ -166,3 +177,21 @@ def omega_pml(e: np.ndarray, gx, gy, fhat, Q, sigma_x, sigma_y=None):
     ey = e[:, 1].astype(np.float64).reshape(-1, 1, 1)
     return -(sigma_y * ex * gx + sigma_x * ey * gy + (sigma_x + sigma_y) * fhat
              + sigma_x * sigma_y * Q)
+
+
+def link_difference(QG: np.ndarray, e: np.ndarray, M: int, Ly: int, Lx: int) -> np.ndarray:
+    """Q_i(x + e_i) - Q_i(x) for every node x of F, shape (q, Ly, Lx); QG is Q on the whole
+    grid G = F + M boundary layers, shape (q, Ly + 2M, Lx + 2M) (node (x, y) of F at
+    [M + y, M + x])."""
+    out = np.empty((QG.shape[0], Ly, Lx))
+    for i, (ex, ey) in enumerate(e):
+        ahead = QG[i, M + ey:M + ey + Ly, M + ex:M + ex + Lx]
+        here = QG[i, M:M + Ly, M:M + Lx]
+        out[i] = ahead - here
+    return out
+
+
+def omega_pml_link_terms(link, fhat, Q, sigma):
+    """The three parts of Eq. (PMLCOLL) with c_i . grad Q_i replaced by the link difference
+    `link` (q, Ly, Lx): -sigma link, -2 sigma f_hat, -sigma^2 Q."""
+    return (-sigma * link, -2.0 * sigma * fhat, -(sigma * sigma) * Q)

@@ -13,7 +13,9 @@ State after n steps: f^n on G, post-stream with Gamma already set by the BC. One
   1. moments U^n on G                                      Eq. (macro)
   2. f_eq^n on G                                           Eqs. (feq-2..4)
   3. on P + ring: f_hat^n = f_eq^n - f_eq_bar, Q^n by the trapezoidal rule
+     (option pml_grad = "link": on all of G, boundary band included)
   4. on P: grad Q^n and Omega^PML                          Eqs. (PMLCOLL), (FD-dx-*)
+     (option "link": c_i . grad Q_i as Q_i(x + e_i) - Q_i(x), pml.py)
   5. collide: f* = f - (f - f_eq)/tau on G, + Omega^PML on P      Eq. (lbe)
   6. stream (pull): f^(n+1)(x) = f*(x - e_i) for x in F
   7. boundary: Gamma of f^(n+1) from
@@ -38,11 +40,22 @@ from .stencil import lattice
 EDGES = ("W", "E", "S", "N")
 
 
+def rk4_step(y0, rate, dt):
+    """One step of the classical fourth-order Runge-Kutta method for the autonomous system
+    dy/dt = rate(y): stages k1 = rate(y0), k2 = rate(y0 + dt k1 / 2), k3 = rate(y0 + dt k2 / 2),
+    k4 = rate(y0 + dt k3); y1 = y0 + dt (k1 + 2 k2 + 2 k3 + k4) / 6."""
+    k1 = rate(y0)
+    k2 = rate(y0 + 0.5 * dt * k1)
+    k3 = rate(y0 + 0.5 * dt * k2)
+    k4 = rate(y0 + dt * k3)
+    return y0 + dt * (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0
+
+
 class OracleLBM:
     def __init__(self, nx, ny, W, tau, sigma_max=0.0, sigma_power=2, bc="zg", q=37,
                  nrbc_edges=(0, 0, 0, 0), beta=0.0, mean=(1.0, 0.0, 0.0, 1.0),
                  relax_sign=-1.0, pml_on=True, Wy=None, periodic_y=False, sigma_split=False,
-                 pml_source=0):
+                 pml_source=0, pml_grad="central"):
         """W: PML layers on every edge, or on the W and E edges when Wy (S and N edges) is
         given, or a per-edge tuple (W_w, W_e, W_s, W_n). periodic_y: the y axis wraps (no PML
         on it; Wy defaults to 0 then); the x edges keep the chosen BC. sigma_split: the
@@ -52,6 +65,11 @@ class OracleLBM:
         + 8: the sign printed there instead of the collision term's."""
         self.lat = lattice(q)
         self.pml_on = pml_on
+        if pml_grad not in ("central", "link"):
+            raise ValueError("pml_grad is 'central' or 'link'")
+        if pml_grad == "link" and sigma_split:
+            raise ValueError("the link-integrated gradient is defined for sigma_x = sigma_y")
+        self.pml_grad = pml_grad
         self.periodic_y = bool(periodic_y)
         if self.periodic_y and Wy is None and np.ndim(W) == 0:
             Wy = 0
@@ -148,6 +166,15 @@ class OracleLBM:
         prim = ch.conserved_to_primitive_rate(mass, mom, energy, Uf)     # (Ly, Lx, 4)
         return {"W": prim[:, 0], "E": prim[:, -1], "S": prim[0, :], "N": prim[-1, :]}
 
+    def _set_sources(self, parts, rho, u, T):
+        """Appendix sources from the three parts (gradient, f_hat, Q) of Omega^PML on F."""
+        sel = sum(pt for k, pt in enumerate(parts) if self.pml_source >> k & 1)
+        M = self.M
+        Uf = np.stack([rho, u[0], u[1], T], axis=-1)[M:M + self.Ly, M:M + self.Lx]
+        if self.pml_source & 8:                          # printed "+" of Eq. NSF-CHAR-PML
+            sel = -sel
+        self._src = self._edge_sources(np.where(self.in_P, sel, 0.0), Uf)
+
     def _target_rates(self, V, U):
         """dU/dt of every edge-band node for the boundary state V (dict edge -> M layers of
         (m, 4) arrays) and the time-n fluid moments U (Ly, Lx, 4) on F."""
@@ -188,18 +215,23 @@ class OracleLBM:
         the fluid moments frozen at time n. (Explicit Euler with the one-sided difference is
         unstable here: its self-coefficient 1 - 3 nu / 2 leaves the unit disc once the
         acoustic CFL nu = (|u_n| + c) / r exceeds 4/3, i.e. already near Mach 0.2.)"""
-        V0 = self.Utgt
+        edges = self.edges
+        names = [(e, j) for e in edges for j in range(len(self.Utgt[e]))]
 
-        def axpy(a, K):
-            return {e: [v + a * kk for v, kk in zip(V0[e], K[e])] for e in self.edges}
+        sizes = [len(self.Utgt[e][j]) for e, j in names]
+        offs = np.concatenate([[0], np.cumsum(sizes)])
 
-        k1 = self._target_rates(V0, U)
-        k2 = self._target_rates(axpy(0.5, k1), U)
-        k3 = self._target_rates(axpy(0.5, k2), U)
-        k4 = self._target_rates(axpy(1.0, k3), U)
-        self.Utgt = {e: [v + (a + 2.0 * b + 2.0 * c + d) / 6.0
-                         for v, a, b, c, d in zip(V0[e], k1[e], k2[e], k3[e], k4[e])]
-                     for e in self.edges}
+        def pack(V):
+            return np.concatenate([V[e][j] for e, j in names])
+
+        def unpack(X):
+            V = {e: [] for e in edges}
+            for k, (e, j) in enumerate(names):
+                V[e].append(X[offs[k]:offs[k + 1]])
+            return V
+
+        X = rk4_step(pack(self.Utgt), lambda X: pack(self._target_rates(unpack(X), U)), 1.0)
+        self.Utgt = unpack(X)
 
     # ---------------------------------------------------------------- public
     def init(self, rho, ux, uy, T):
@@ -230,7 +262,21 @@ class OracleLBM:
             rho, u, T = moments(f, lat.xi)                                   # 1
             fe = self._feq(rho, u, T)                                        # 2
             fstar = bgk(f, fe, self.tau)                                     # 5 (BGK part)
-            if any(self.widths) and self.pml_on:
+            if any(self.widths) and self.pml_on and self.pml_grad == "link":
+                Fs = self.Fs
+                fhatG = fe - self.fbar[:, None, None]                        # 3, on all of G
+                if self.Q is None:
+                    QG = np.zeros_like(fhatG)                                # Q^0 = 0
+                else:
+                    QG = pml.trapezoid_update(self.Q, self.fhat_prev, fhatG)
+                self.Q, self.fhat_prev = QG, fhatG
+                link = pml.link_difference(QG, lat.e, self.M, self.Ly, self.Lx)      # 4
+                parts = pml.omega_pml_link_terms(link, fhatG[Fs], QG[Fs], self.sigma_x)
+                om = parts[0] + parts[1] + parts[2]
+                fstar[Fs] = fstar[Fs] + np.where(self.in_P, om, 0.0)         # 5 (PML part)
+                if self.bc == "nrbc" and self.pml_source & 7:
+                    self._set_sources(parts, rho, u, T)
+            elif any(self.widths) and self.pml_on:
                 Fs = self.Fs
                 fhat = np.where(self.qsup, fe[Fs] - self.fbar[:, None, None], 0.0)   # 3
                 if self.Q is None:
@@ -245,12 +291,7 @@ class OracleLBM:
                 if self.bc == "nrbc" and self.pml_source & 7:
                     parts = pml.omega_pml_terms(lat.e, gx, gy, fhat, Q, self.sigma_x,
                                                 self.sigma_y)
-                    sel = sum(pt for k, pt in enumerate(parts) if self.pml_source >> k & 1)
-                    M = self.M
-                    Uf = np.stack([rho, u[0], u[1], T], axis=-1)[M:M + self.Ly, M:M + self.Lx]
-                    if self.pml_source & 8:                  # printed "+" of Eq. NSF-CHAR-PML
-                        sel = -sel
-                    self._src = self._edge_sources(np.where(self.in_P, sel, 0.0), Uf)
+                    self._set_sources(parts, rho, u, T)
             if self.periodic_y:
                 # the rows beyond a periodic y axis carry the post-collision populations of
                 # the rows they image (PML term included), as on an unbounded periodic lattice
