@@ -97,6 +97,16 @@ typedef struct {
   int periodic_y;               /* 1: the y axis is periodic (Sec. 5.1 setting): no S / N    */
                                 /* boundary and no PML there (with use_pml_widths = 0 the    */
                                 /* S / N widths are taken as 0; otherwise they must be 0)    */
+  int pml_grad;                 /* 0: c_i . grad Q_i of Eq. (PMLCOLL) by the printed per-axis */
+                                /* differences, Eqs. (FD-dx-center) / (FD-dx-bw) (default).  */
+                                /* 1: by the link difference Q_i(x + e_i) - Q_i(x), the     */
+                                /* integral of c_i . grad Q_i along the path the population  */
+                                /* travels in one step. Not the paper's printed scheme: an   */
+                                /* option, because the printed differences let grid-scale    */
+                                /* modes grow for every sigma > 0 (fast for D2Q37), while    */
+                                /* the link form stays stable. Q is then also integrated on  */
+                                /* the M-node bulk ring next to the PML and on every boundary */
+                                /* node outside F. Needs split = 0 (sigma_x = sigma_y).      */
 } lbm_bc_params;
 
 /* Create a context. tau > 1/2 (tau = +INFINITY gives collisionless free streaming);

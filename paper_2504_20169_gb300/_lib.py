@@ -32,7 +32,7 @@ class lbm_bc_params(C.Structure):
     _fields_ = [("edge", C.c_int * 4), ("beta", C.c_double), ("relax_sign", C.c_double),
                 ("rho0", C.c_double), ("u0x", C.c_double), ("u0y", C.c_double),
                 ("T0", C.c_double), ("use_pml_widths", C.c_int), ("pml_widths", C.c_int * 4),
-                ("pml_source", C.c_int), ("periodic_y", C.c_int)]
+                ("pml_source", C.c_int), ("periodic_y", C.c_int), ("pml_grad", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)

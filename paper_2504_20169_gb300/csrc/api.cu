@@ -297,7 +297,7 @@ lbm_status lbm_lattice_info(lbm_stencil stencil, int* q, int* e, double* w, doub
 }
 
 // Storage geometry of a grid (section "Storage" of lbm_device.cuh) and the bytes it needs.
-static Geom make_geom(int nx, int ny, const int W[4], int M, int py) {
+static Geom make_geom(int nx, int ny, const int W[4], int M, int py, int link) {
   Geom g{};
   g.nx = nx;
   g.ny = ny;
@@ -312,18 +312,22 @@ static Geom make_geom(int nx, int ny, const int W[4], int M, int py) {
   g.cF0 = 32;
   g.pitch = ((g.cF0 + g.Lx + g.M) + 31) / 32 * 32;
   g.plane = ((long long)g.pitch * (g.Ly + 2 * g.M) + 63) / 64 * 64;
-  // the frame holds the PML and its inner ring, and at least the two outer layers whose
-  // moments the characteristic targets read (so also for D2Q9, M = 1)
-  auto depth = [&](int w) { return std::max(w > 0 ? w + 1 : 0, std::max(g.M, 2)); };
+  // the frame holds the PML and its inner ring (1 node for the printed central difference, M
+  // for the link difference), and at least the two outer layers whose moments the
+  // characteristic targets read (so also for D2Q9, M = 1)
+  g.link = link;
+  g.qr = link ? M : 1;
+  auto depth = [&](int w) { return std::max(w > 0 ? w + g.qr : 0, std::max(g.M, 2)); };
   g.Fw = depth(g.Ww);
   g.Fe = depth(g.We);
   g.Fs = py ? 0 : depth(g.Ws);
   g.Fn = py ? 0 : depth(g.Wn);
   g.frame_n = (g.Fs + g.Fn) * g.Lx + (g.Ly - g.Fs - g.Fn) * (g.Fw + g.Fe);
-  g.Sp = has_pml(g) ? ((long long)g.frame_n + 31) / 32 * 32 : 0;
   g.nb = 2 * g.M * (g.Lx + g.Ly);
   g.ne = 4 * (g.Lx + g.Ly);
   g.ngamma = 2 * g.M * (g.Lx + 2 * g.M) + 2 * g.M * g.Ly;
+  // accumulator slots: the frame, then (link mode) the boundary nodes outside F
+  g.Sp = has_pml(g) ? ((long long)g.frame_n + (link ? g.ngamma : 0) + 31) / 32 * 32 : 0;
   return g;
 }
 
@@ -345,7 +349,7 @@ extern "C" lbm_status lbm_estimate_bytes(const lbm_grid* grid, lbm_stencil stenc
       (precision != LBM_FP64 && precision != LBM_FP32_DEV))
     return LBM_EINVAL;
   const int W4[4] = {pml_width, pml_width, pml_width, pml_width};
-  const Geom g = make_geom(grid->nx, grid->ny, W4, halo_of(q), 0);
+  const Geom g = make_geom(grid->nx, grid->ny, W4, halo_of(q), 0, 0);
   *bytes = bytes_of(g, q, precision == LBM_FP64 ? 8 : 4);
   return LBM_OK;
 }
@@ -384,6 +388,8 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   if (bp.periodic_y && (W4[2] || W4[3])) return fail("a periodic y axis has no PML");
   if (bp.periodic_y && bc == LBM_BC_PERIODIC) return fail("periodic_y needs a ZG or NRBC x edge");
   if (bp.pml_source < 0 || bp.pml_source > 15) return fail("pml_source is a bitmask of 1, 2, 4, 8");
+  if (bp.pml_grad != 0 && bp.pml_grad != 1) return fail("pml_grad must be 0 or 1");
+  if (bp.pml_grad == 1 && sg.split) return fail("the link gradient needs sigma_x = sigma_y");
   if (!(bp.rho0 > 0) || !(bp.T0 > 0) || !std::isfinite(bp.u0x) || !std::isfinite(bp.u0y) ||
       !std::isfinite(bp.beta))
     return fail("bad mean state or beta");
@@ -405,7 +411,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   if (!lattice_of(q, ctx->w, &ctx->r, lerr)) { delete ctx; return fail("quadrature failed"); }
   cudaGetDevice(&ctx->device);
 
-  ctx->g = make_geom(grid->nx, grid->ny, W4, halo_of(q), bp.periodic_y);
+  ctx->g = make_geom(grid->nx, grid->ny, W4, halo_of(q), bp.periodic_y, bp.pml_grad);
   Geom& g = ctx->g;
 
   switch (q * 2 + (precision == LBM_FP32_DEV)) {
@@ -816,7 +822,7 @@ lbm_status lbm_checkpoint(lbm_ctx* ctx, void* host, size_t bytes) {
   CkptHeader h{kMagic, ctx->q, ctx->g.nx, ctx->g.ny, pack_widths(ctx), (int64_t)ctx->prec,
                ctx->steps,
                (int64_t)(ctx->prev_valid ? 1 : 0) | (int64_t)(ctx->prev_prestream ? 2 : 0) |
-                   ((int64_t)ctx->g.py << 2)};
+                   ((int64_t)ctx->g.py << 2) | ((int64_t)ctx->g.link << 3)};
   std::memcpy(p, &h, sizeof h);
   p += sizeof h;
   const cudaMemcpyKind k = cudaMemcpyDeviceToHost;
@@ -845,7 +851,7 @@ lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes) {
   std::memcpy(&h, p, sizeof h);
   if (h.magic != kMagic || h.q != ctx->q || h.nx != ctx->g.nx || h.ny != ctx->g.ny ||
       h.widths != pack_widths(ctx) || h.prec != (int64_t)ctx->prec ||
-      ((h.flags >> 2) & 1) != ctx->g.py) {
+      ((h.flags >> 2) & 1) != ctx->g.py || ((h.flags >> 3) & 1) != ctx->g.link) {
     ctx->err = "checkpoint does not match this context";
     return LBM_EINVAL;
   }

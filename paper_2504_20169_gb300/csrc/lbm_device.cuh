@@ -37,11 +37,16 @@ struct Geom {
   int pitch;         // storage row length (elements), multiple of 32
   int cF0;           // storage column of x = 0 of F, multiple of 32
   long long plane;   // elements per direction plane (pitch * (Ly + 2M))
-  int Fw, Fe, Fs, Fn; // frame depth per edge: max(W_edge + 1, M, 2) with a PML there, else
+  int Fw, Fe, Fs, Fn; // frame depth per edge: max(W_edge + qr, M, 2) with a PML there, else
                      // max(M, 2) (the two outer layers feed the characteristic targets);
                      // Fs = Fn = 0 on a periodic y axis
   int frame_n;       // number of frame nodes
-  long long Sp;      // PML accumulator stride per direction
+  int link;          // 1: c_i . grad Q_i as the link difference Q_i(x + e_i) - Q_i(x) (an
+                     // option; 0: the printed per-axis differences, Eqs. FD-dx-center / -bw)
+  int qr;            // depth of the ring of bulk nodes next to P that carries Q: 1 (printed
+                     // central difference), M (link difference)
+  long long Sp;      // PML accumulator stride per direction: the frame nodes, then (link
+                     // mode) the ngamma boundary nodes outside F
   int nb;            // characteristic-BC band nodes: 2 M (Lx + Ly)
   int ne;            // saved fluid-moment slots: 4 (Lx + Ly) (two layers per edge)
   int ngamma;        // boundary nodes outside F: 2M(Lx + 2M) + 2M Ly
@@ -79,7 +84,8 @@ __device__ inline int dist_out(const Geom& g, int x, int y) {
 // PML classification of node (x, y) of F. Layer index along x: i = W_w - x near the W edge,
 // x - (Lx - 1 - W_e) near the E edge, 0 between (likewise along y with W_s, W_n); layer
 // fraction f_x = i / (width of that edge). P = {f_x > 0 or f_y > 0}; the accumulator Q is kept
-// on P and on the ring one node inside each PML edge.
+// on P and on the ring of qr nodes inside each PML edge (in link mode also on every boundary
+// node outside F, see q_slot).
 template <class Real>
 struct PmlNode {
   bool has_q, in_p;
@@ -93,8 +99,9 @@ __device__ inline PmlNode<Real> pml_node(const Geom& g, int x, int y) {
   const int is = g.Ws > 0 ? max(0, g.Ws - y) : 0, in = g.Wn > 0 ? max(0, g.Wn - ey) : 0;
   PmlNode<Real> n;
   n.in_p = (iw | ie | is | in) > 0;
-  n.has_q = (g.Ww > 0 && x <= g.Ww) || (g.We > 0 && ex <= g.We) || (g.Ws > 0 && y <= g.Ws) ||
-            (g.Wn > 0 && ey <= g.Wn);
+  const int r = g.qr - 1;
+  n.has_q = (g.Ww > 0 && x <= g.Ww + r) || (g.We > 0 && ex <= g.We + r) ||
+            (g.Ws > 0 && y <= g.Ws + r) || (g.Wn > 0 && ey <= g.Wn + r);
   n.fx = iw > 0 ? Real(iw) / Real(g.Ww) : (ie > 0 ? Real(ie) / Real(g.We) : Real(0));
   n.fy = is > 0 ? Real(is) / Real(g.Ws) : (in > 0 ? Real(in) / Real(g.Wn) : Real(0));
   return n;
@@ -481,6 +488,38 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
   if (!pn.in_p) return;
   Real sx, sy;
   pml_sigmas(c, pn, sx, sy);
+  if (g.link) {
+    // link mode: sigma (Q_i(x + e_i) - Q_i(x)), the integral of sigma c_i . grad Q_i along the
+    // link the population travels (sigma_x = sigma_y); Q = (S^(n-1) + S^n) / 2 on the frame
+    // and on the boundary nodes outside F
+    const long long idx = gindex(g, x, y);
+    const bool src = (src_mask & 1) && outermost(g, x, y);   // Appendix term I
+    Real smom[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+    for (int i = 0; i < S::Q; ++i) {
+      if (S::ex(i) == 0 && S::ey(i) == 0) continue;
+      const Real* so = Sold + (long long)i * g.Sp;
+      const Real* sn = Snew + (long long)i * g.Sp;
+      const int nb = q_slot(g, x + S::ex(i), y + S::ey(i));
+      const Real gq = sx * ((__ldg(so + nb) + __ldg(sn + nb)) - (__ldg(so + fi) + __ldg(sn + fi)));
+      Real* b = B + (long long)i * g.plane + idx;
+      *b = *b - Real(0.5) * gq;
+      if (src) {
+        const Real part = -Real(0.5) * gq;
+        smom[0] += part;
+        smom[1] += Real(S::ex(i)) * part;
+        smom[2] += Real(S::ey(i)) * part;
+        smom[3] += Real(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
+      }
+    }
+    if (src) {
+      smom[1] *= c.r;
+      smom[2] *= c.r;
+      smom[3] *= Real(0.5) * c.r2;
+      put_pml_source(g, Sedge, x, y, smom, true);
+    }
+    return;
+  }
   // x axis: neighbours / one-sided stencil
   int ax0, ax1, ax2;  // frame indices; derivative = cx0*Q(ax0) + cx1*Q(ax1) + cx2*Q(ax2)
   Real cx0, cx1, cx2;
@@ -560,16 +599,36 @@ __device__ inline void gamma_xy(const Geom& g, int t, int& x, int& y) {
   x = k < M ? k - M : g.Lx + (k - M);
 }
 
+// Inverse of gamma_xy: index of a boundary node (x, y) outside F.
+__device__ inline int gamma_index(const Geom& g, int x, int y) {
+  const int M = g.M, Gx = g.Lx + 2 * M;
+  if (y < 0) return (y + M) * Gx + (x + M);
+  if (y >= g.Ly) return M * Gx + (y - g.Ly) * Gx + (x + M);
+  return 2 * M * Gx + y * 2 * M + (x < 0 ? x + M : M + (x - g.Lx));
+}
+
+// Slot of node (x, y) of G in the accumulator arrays in link mode: its frame index inside F,
+// frame_n + its boundary index outside F; along a periodic y axis y is wrapped first.
+__device__ inline int q_slot(const Geom& g, int x, int y) {
+  if (g.py) y = y < 0 ? y + g.Ly : (y >= g.Ly ? y - g.Ly : y);
+  if (x >= 0 && x < g.Lx && y >= 0 && y < g.Ly) return frame_index(g, x, y);
+  return g.frame_n + gamma_index(g, x, y);
+}
+
 // Boundary layers outside F (Sec. 4): the post-stream populations there are set by the BC and
 // then BGK-collided (no PML term). Zero gradient (Eq. zg-bc): copy of the nearest fluid node x_f,
 // so the result equals the BGK post-collision of x_f. Characteristic BC on the edge bands:
 // f = f_eq(U_tgt) + f_neq(x_f), whose moments are U_tgt, so the collided value is
 // f_eq(U_tgt) + (1 - omega) f_neq(x_f); the corner blocks use the zero-gradient copy.
 // Periodic: the post-collision value of the periodic image.
+// Link mode with a PML (Sold != nullptr): the node also advances its accumulator
+// S^n = S^(n-1) + f_hat^n (slot frame_n + t) from the moments of its pre-collision state.
 template <class S, class Real, bool DEV, bool STREAM>
 __global__ void __launch_bounds__(128) k_gamma(Geom g, Consts<Real> c, BcParams bc,
                                                const Real* __restrict__ A, Real* __restrict__ B,
-                                               const double* __restrict__ Vtgt) {
+                                               const double* __restrict__ Vtgt,
+                                               const Real* __restrict__ Sold,
+                                               Real* __restrict__ Snew) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.ngamma) return;
   int x, y;
@@ -613,9 +672,22 @@ __global__ void __launch_bounds__(128) k_gamma(Geom g, Consts<Real> c, BcParams 
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       const Real neq = p[i] - eq_dir<S, Real, DEV>(i, m, kf, c);
-      B[(long long)i * g.plane + dst] = eq_dir<S, Real, DEV>(i, mt, kt, c) + keep * neq;
+      const Real eqt = eq_dir<S, Real, DEV>(i, mt, kt, c);
+      B[(long long)i * g.plane + dst] = eqt + keep * neq;
+      if (Sold) {
+        const long long k = (long long)i * g.Sp + g.frame_n + t;
+        Snew[k] = Sold[k] + (eqt - c.eqbar[i]);
+      }
     }
     return;
+  }
+  if (Sold) {
+    const EqCoef<Real> kf = eq_coef<S::ORDER, Real>(m);
+#pragma unroll
+    for (int i = 0; i < S::Q; ++i) {
+      const long long k = (long long)i * g.Sp + g.frame_n + t;
+      Snew[k] = Sold[k] + (eq_dir<S, Real, DEV>(i, m, kf, c) - c.eqbar[i]);
+    }
   }
   collide_bgk<S, Real, DEV>(p, m, c);
 #pragma unroll

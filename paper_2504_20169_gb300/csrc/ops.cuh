@@ -41,6 +41,35 @@ __global__ void k_init_eq(Geom g, Consts<Real> c, const double* __restrict__ rho
   }
 }
 
+// Link mode: the accumulator of the boundary nodes outside F, S^(-1) = -f_hat^0 / 2 with f_hat^0
+// from the fields at the nearest fluid node (the state the boundary rule gives those nodes at
+// initialization: zero-gradient copy, or characteristic targets equal to the fields there).
+template <class S, class Real, bool DEV>
+__global__ void k_init_gamma_s(Geom g, Consts<Real> c, const double* __restrict__ rho,
+                               const double* __restrict__ ux, const double* __restrict__ uy,
+                               const double* __restrict__ T, Real* __restrict__ Sold) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.ngamma) return;
+  int x, y;
+  gamma_xy(g, t, x, y);
+  if (g.py && (y < 0 || y >= g.Ly)) return;   // images of rows inside F (wrapped lookups)
+  const int k = min(max(y, 0), g.Ly - 1) * g.Lx + min(max(x, 0), g.Lx - 1);
+  const double r0 = rho[k], vx = ux[k], vy = uy[k], T0 = T[k];
+  Macro<Real> m;
+  m.rho = Real(r0);
+  m.drho = Real(r0 - 1.0);
+  m.inv_rho = Real(1.0 / r0);
+  m.urx = c.r * Real(vx);
+  m.ury = c.r * Real(vy);
+  m.u2 = Real(vx * vx + vy * vy);
+  m.theta = Real(T0 - 1.0);
+  const EqCoef<Real> kc = eq_coef<S::ORDER, Real>(m);
+#pragma unroll
+  for (int i = 0; i < S::Q; ++i)
+    Sold[(long long)i * g.Sp + g.frame_n + t] =
+        Real(-0.5) * (eq_dir<S, Real, DEV>(i, m, kc, c) - c.eqbar[i]);
+}
+
 // Block-wide reduction of NV doubles (sums, except slots flagged in min_mask which take the
 // minimum); thread 0 writes the block's partials.
 template <int NV>
@@ -180,8 +209,11 @@ struct Ops {
     Real* B = static_cast<Real*>(d.B);
     // characteristic targets then boundary band on bs, PML frame on fs, interior on d.st; all
     // read A and write disjoint parts of B
+    const bool link = g.link && has_pml(g);
     const cudaStream_t bs = d.aux ? d.aux : d.st;
-    const cudaStream_t fs = d.aux2 ? d.aux2 : bs;
+    // link mode: the gradient pass reads the boundary nodes' new accumulator, so the frame
+    // runs on the boundary stream in the order frame phase 1, band, frame phase 2
+    const cudaStream_t fs = link ? bs : (d.aux2 ? d.aux2 : bs);
     auto mark = [&](int k, cudaStream_t s) {
       if (d.ev) cudaEventRecord(d.ev[k], s);
     };
@@ -198,7 +230,7 @@ struct Ops {
     mark(4, fs);
     bool fused = false;
     if constexpr (DEV) {
-      if (has_pml(g)) {
+      if (has_pml(g) && !link) {
         // FP32: single-pass frame (tile + halo in shared memory)
         const FrameTiles ft = make_frame_tiles(g, 256);
         const size_t smem = pml_fused_smem<S>(ft);
@@ -213,16 +245,21 @@ struct Ops {
           g, c, A, B, static_cast<const Real*>(d.Sold), static_cast<Real*>(d.Snew), d.Uedge_out,
           d.bc.bc == 2 ? 1 : 0, d.flag, d.Sedge_out, src_mask);
     mark(5, fs);
+    auto band = [&]() {
+      mark(8, bs);
+      k_gamma<S, Real, DEV, STREAM><<<(g.ngamma + 127) / 128, 128, 0, bs>>>(
+          g, c, d.bc, A, B, d.Vtgt, link ? static_cast<const Real*>(d.Sold) : nullptr,
+          link ? static_cast<Real*>(d.Snew) : nullptr);
+      mark(9, bs);
+    };
+    if (link) band();
     mark(6, fs);
     if (has_pml(g) && !fused)
       k_frame2<S, Real><<<(g.frame_n + 127) / 128, 128, 0, fs>>>(
           g, c, B, static_cast<const Real*>(d.Sold), static_cast<const Real*>(d.Snew),
           d.Sedge_out, src_mask);
     mark(7, fs);
-    mark(8, bs);
-    k_gamma<S, Real, DEV, STREAM><<<(g.ngamma + 127) / 128, 128, 0, bs>>>(g, c, d.bc, A, B,
-                                                                          d.Vtgt);
-    mark(9, bs);
+    if (!link) band();
     const int nbx = (g.Lx - g.Fe - (g.Fw / 32) * 32 + 31) / 32;
     const int ny_in = g.Ly - g.Fs - g.Fn;
     constexpr int BY = 4;
@@ -258,6 +295,9 @@ struct Ops {
     k_init_eq<S, Real, DEV><<<grid, 128, 0, d.st>>>(g, consts(d), rho, ux, uy, T,
                                                    static_cast<Real*>(const_cast<void*>(d.A)),
                                                    static_cast<Real*>(const_cast<void*>(d.Sold)));
+    if (g.link && has_pml(g))
+      k_init_gamma_s<S, Real, DEV><<<(g.ngamma + 127) / 128, 128, 0, d.st>>>(
+          g, consts(d), rho, ux, uy, T, static_cast<Real*>(const_cast<void*>(d.Sold)));
     return cudaGetLastError();
   }
 

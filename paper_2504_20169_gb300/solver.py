@@ -41,11 +41,12 @@ class Solver:
     def __init__(self, nx, ny, W, tau, sigma_max=0.0, sigma_power=2, bc="zg", q=37,
                  nrbc_edges=(0, 0, 0, 0), beta=0.0, mean=(1.0, 0.0, 0.0, 1.0), relax_sign=-1.0,
                  precision="fp64", stream=None, pml_widths=None, periodic_y=False,
-                 sigma_split=False, pml_source=0):
+                 sigma_split=False, pml_source=0, pml_grad="central"):
         """W: PML layers on every edge, unless pml_widths = (W_w, W_e, W_s, W_n) is given;
         periodic_y: the y axis wraps (no S/N boundary, no PML there); sigma_split: the
         sigma_x != sigma_y form of Eq. (pml-general); pml_source: bitmask of the Appendix PML
-        source terms I (1), II (2), III (4) added to the characteristic targets."""
+        source terms I (1), II (2), III (4) added to the characteristic targets; pml_grad:
+        "central" (the printed differences) or "link" (Q_i(x + e_i) - Q_i(x))."""
         import torch
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -65,6 +66,7 @@ class Solver:
                 bp.pml_widths[k] = int(pml_widths[k])
         bp.periodic_y = 1 if periodic_y else 0
         bp.pml_source = int(pml_source)
+        bp.pml_grad = {"central": 0, "link": 1}[pml_grad]
         out = C.c_void_p()
         with torch.cuda.device(self.stream.device):
             _check(L.lib().lbm_create(C.byref(grid), q, float(tau), W, C.byref(sig), _BC[bc],

@@ -8,7 +8,7 @@ from oracle import OracleLBM
 def case_kwargs(**kw):
     base = dict(nx=32, ny=32, W=4, tau=0.8, sigma_max=0.1, sigma_power=3, bc="zg", q=37,
                 nrbc_edges=(0, 0, 0, 0), beta=0.0, mean=(1.0, 0.0, 0.0, 1.0), relax_sign=-1.0,
-                widths=None, periodic_y=False, split=False, pml_source=0)
+                widths=None, periodic_y=False, split=False, pml_source=0, pml_grad="central")
     base.update(kw)
     return base
 
@@ -19,7 +19,7 @@ def run_oracle(kw, fields, steps):
                   kw["bc"], q=kw["q"], nrbc_edges=kw["nrbc_edges"], beta=kw["beta"],
                   mean=kw["mean"], relax_sign=kw["relax_sign"],
                   periodic_y=kw["periodic_y"], sigma_split=kw["split"],
-                  pml_source=kw["pml_source"])
+                  pml_source=kw["pml_source"], pml_grad=kw["pml_grad"])
     o.init(*fields)
     o.step(steps)
     return o.fields(), o
@@ -31,7 +31,7 @@ def make_solver(kw, precision="fp64"):
                   kw["bc"], kw["q"], kw["nrbc_edges"], kw["beta"], kw["mean"],
                   kw["relax_sign"], precision, pml_widths=kw["widths"],
                   periodic_y=kw["periodic_y"], sigma_split=kw["split"],
-                  pml_source=kw["pml_source"])
+                  pml_source=kw["pml_source"], pml_grad=kw["pml_grad"])
 
 
 def run_gpu(kw, fields, steps, precision="fp64"):
