@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
   // Appendix PML source at the outermost layer: moments of the f_hat (II) and Q (III) parts
   // here; the gradient part (I) is added by k_frame2
   const bool src = src_mask && outermost(g, x, y);
-  Real smom[4] = {Real(0), Real(0), Real(0), Real(0)};
+  double smom[4] = {0.0, 0.0, 0.0, 0.0};   // FP64 sums (cancellation)
   if (has_q) {
     // all accumulator loads in flight before any store
     Real so[S::Q];
@@ -450,12 +450,12 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
       if (in_p) out = out - (ssum * fhat + sprod * q);
       B[(long long)i * g.plane + idx] = out;
       if (src && in_p) {
-        const Real part = -(((src_mask & 2) ? ssum * fhat : Real(0)) +
-                            ((src_mask & 4) ? sprod * q : Real(0)));
+        const double part = -(((src_mask & 2) ? double(ssum) * double(fhat) : 0.0) +
+                              ((src_mask & 4) ? double(sprod) * double(q) : 0.0));
         smom[0] += part;
-        smom[1] += Real(S::ex(i)) * part;
-        smom[2] += Real(S::ey(i)) * part;
-        smom[3] += Real(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
+        smom[1] += double(S::ex(i)) * part;
+        smom[2] += double(S::ey(i)) * part;
+        smom[3] += double(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
       }
     }
   } else {
@@ -465,9 +465,9 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
   }
   if (src) {
     // lattice moments -> physical: xi = r e, |xi|^2 / 2 = r^2 |e|^2 / 2
-    smom[1] *= c.r;
-    smom[2] *= c.r;
-    smom[3] *= Real(0.5) * c.r2;
+    smom[1] *= double(c.r);
+    smom[2] *= double(c.r);
+    smom[3] *= 0.5 * double(c.r2);
     put_pml_source(g, Sedge, x, y, smom, false);
   }
 }
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
     // and on the boundary nodes outside F
     const long long idx = gindex(g, x, y);
     const bool src = (src_mask & 1) && outermost(g, x, y);   // Appendix term I
-    Real smom[4] = {Real(0), Real(0), Real(0), Real(0)};
+    double smom[4] = {0.0, 0.0, 0.0, 0.0};   // FP64 sums (cancellation)
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       if (S::ex(i) == 0 && S::ey(i) == 0) continue;
@@ -505,17 +505,17 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
       Real* b = B + (long long)i * g.plane + idx;
       *b = *b - Real(0.5) * gq;
       if (src) {
-        const Real part = -Real(0.5) * gq;
+        const double part = -0.5 * double(gq);
         smom[0] += part;
-        smom[1] += Real(S::ex(i)) * part;
-        smom[2] += Real(S::ey(i)) * part;
-        smom[3] += Real(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
+        smom[1] += double(S::ex(i)) * part;
+        smom[2] += double(S::ey(i)) * part;
+        smom[3] += double(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
       }
     }
     if (src) {
-      smom[1] *= c.r;
-      smom[2] *= c.r;
-      smom[3] *= Real(0.5) * c.r2;
+      smom[1] *= double(c.r);
+      smom[2] *= double(c.r);
+      smom[3] *= 0.5 * double(c.r2);
       put_pml_source(g, Sedge, x, y, smom, true);
     }
     return;
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
   }
   const long long idx = gindex(g, x, y);
   const bool src = (src_mask & 1) && outermost(g, x, y);   // Appendix term I
-  Real smom[4] = {Real(0), Real(0), Real(0), Real(0)};
+  double smom[4] = {0.0, 0.0, 0.0, 0.0};   // FP64 sums (cancellation)
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) {
     const Real* so = Sold + (long long)i * g.Sp;
@@ -573,17 +573,17 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
     Real* b = B + (long long)i * g.plane + idx;
     *b = *b - Real(0.5) * gq;   // Q = (S^(n-1) + S^n) / 2
     if (src) {
-      const Real part = -Real(0.5) * gq;
+      const double part = -0.5 * double(gq);
       smom[0] += part;
-      smom[1] += Real(S::ex(i)) * part;
-      smom[2] += Real(S::ey(i)) * part;
-      smom[3] += Real(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
+      smom[1] += double(S::ex(i)) * part;
+      smom[2] += double(S::ey(i)) * part;
+      smom[3] += double(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
     }
   }
   if (src) {
-    smom[1] *= c.r;
-    smom[2] *= c.r;
-    smom[3] *= Real(0.5) * c.r2;
+    smom[1] *= double(c.r);
+    smom[2] *= double(c.r);
+    smom[3] *= 0.5 * double(c.r2);
     put_pml_source(g, Sedge, x, y, smom, true);
   }
 }

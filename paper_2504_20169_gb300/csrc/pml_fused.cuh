@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   }
   // Appendix PML source at the outermost layer: moments of the selected parts of Omega^PML
   const bool src = src_mask && outermost(g, x, y);
-  float smom[4] = {0.f, 0.f, 0.f, 0.f};
+  double smom[4] = {0.0, 0.0, 0.0, 0.0};   // FP64 sums (cancellation)
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) {
     const float eq = eq_dir<S, float, true>(i, m, kc, c);
@@ -200,20 +200,21 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
       if (S::ey(i) != 0) gq += sx * float(S::ey(i)) * (cy0 * q[oy0] + cy1 * q[oy1] + cy2 * q[oy2]);
       out = out - (gq + ssum * fhat + sprod * qn);
       if (src) {
-        const float part = -(((src_mask & 1) ? gq : 0.f) + ((src_mask & 2) ? ssum * fhat : 0.f) +
-                             ((src_mask & 4) ? sprod * qn : 0.f));
+        const double part = -(((src_mask & 1) ? double(gq) : 0.0) +
+                              ((src_mask & 2) ? double(ssum) * double(fhat) : 0.0) +
+                              ((src_mask & 4) ? double(sprod) * double(qn) : 0.0));
         smom[0] += part;
-        smom[1] += float(S::ex(i)) * part;
-        smom[2] += float(S::ey(i)) * part;
-        smom[3] += float(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
+        smom[1] += double(S::ex(i)) * part;
+        smom[2] += double(S::ey(i)) * part;
+        smom[3] += double(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
       }
     }
     B[(long long)i * g.plane + idx] = out;
   }
   if (src) {
-    smom[1] *= c.r;
-    smom[2] *= c.r;
-    smom[3] *= 0.5f * c.r2;
+    smom[1] *= double(c.r);
+    smom[2] *= double(c.r);
+    smom[3] *= 0.5 * double(c.r2);
     put_pml_source(g, Sedge, x, y, smom, false);
   }
 }

@@ -9,19 +9,13 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from parity_helpers import case_kwargs, field_errors, make_solver, run_gpu, run_oracle
+from parity_helpers import case_kwargs, check as _check, make_solver
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32dev": 1e-5}
-
 
 def check(kw, fields, steps, precision):
-    ora, _ = run_oracle(kw, fields, steps)
-    gpu = run_gpu(kw, fields, steps, precision)
-    full, pert = field_errors(gpu, ora)
-    print(f"link {precision} full={['%.2e' % e for e in full]} pert={['%.2e' % e for e in pert]}")
-    assert max(full) < TOL[precision], full
+    _check(kw, fields, steps, precision, tag="link ")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32dev"])

@@ -170,6 +170,7 @@ class Case:
     nrbc_edges: tuple = (0, 1, 0, 0)   # W, E, S, N: 0 = PNR-LODI, 1 = CBC relax
     beta: float = 0.3
     mean: tuple = (1.0, 0.0, 0.0, 1.0)  # rho0, u0x, u0y, T0 (mean equilibrium of the PML)
+    pml_grad: str = "central"    # "central" (printed differences) | "link" (link difference)
 
     def fields(self):
         if self.ic == "pulse":
