@@ -202,6 +202,38 @@ lbm_status lbm_profile_read(lbm_ctx* ctx, double* ms, int* steps);
 lbm_status lbm_estimate_bytes(const lbm_grid* grid, lbm_stencil stencil, int pml_width,
                               lbm_bc_kind bc, lbm_precision precision, size_t* bytes);
 
+/* Same as lbm_estimate_bytes for the full set of lbm_create arguments that shape the grid:
+ * per-edge PML widths and the periodic y axis (bc_params->use_pml_widths, pml_widths,
+ * periodic_y) and the link gradient's wider accumulator (bc_params->pml_grad); sigma and
+ * bc_params may be NULL as in lbm_create. Runs lbm_create's argument checks (LBM_EINVAL with
+ * lbm_last_error(NULL) set for arguments lbm_create rejects); no allocation, no GPU needed. */
+lbm_status lbm_estimate_bytes_bc(const lbm_grid* grid, lbm_stencil stencil, int pml_width,
+                                 const lbm_sigma_profile* sigma, lbm_bc_kind bc,
+                                 const lbm_bc_params* bc_params, lbm_precision precision,
+                                 size_t* bytes);
+
+/* Diagnostic exports for bit-exact tests of the index maps (no counterpart in the paper; the
+ * maps are those of Eq. (lbe) and of Eqs. (PML_ramp), (pml-general)). Neither needs lbm_init.
+ * lbm_export_pull_index: for every direction i and node (x, y) of F, the grid-G index
+ * gy * (Lx + 2M) + gx of the node the pull of direction i reads, x - e_i, as the kernels compute
+ * it (G coordinates: gx = x + M, gy = y + M); host buffer of q * Lx * Ly int64, layout
+ * [i][y][x]. lbm_export_site_class: per node of F (host buffers of Lx * Ly, layout [y][x], any
+ * may be NULL): layer = the PML layer index max(i_x, i_y) (0 in the bulk), has_q = 1 where the
+ * PML accumulator Q is kept (P and its inner ring), sigma_x / sigma_y = the absorption
+ * coefficients the collision applies (0 off P). Both allocate a temporary device buffer and
+ * synchronize the context stream. */
+lbm_status lbm_export_pull_index(lbm_ctx* ctx, int64_t* host);
+lbm_status lbm_export_site_class(lbm_ctx* ctx, int32_t* layer, uint8_t* has_q, double* sigma_x,
+                                 double* sigma_y);
+
+/* Measured vector FMA throughput of the current CUDA device (no counterpart in the paper: the
+ * ALU roofline of the FP64 path, whose interior kernel is bound by the FP64 pipe). precision
+ * LBM_FP64 times double FMAs, LBM_FP32_DEV float FMAs: every SM filled with threads running
+ * eight independent FMA chains, one warm-up launch, then one timed launch (CUDA events on
+ * cuda_stream, a cudaStream_t or NULL). *tflops = 2 x FMAs / time, *ms = the timed launch
+ * (ms may be NULL). Synchronizes; errors by lbm_last_error(NULL). */
+lbm_status lbm_peak_fma(lbm_precision precision, double* tflops, double* ms, void* cuda_stream);
+
 /* Batched execution of independent instances (serving). A batch holds a resident set of
  * initialized contexts on one device and advances all of them together: each step is one
  * CUDA-graph launch on the batch's stream whose child graphs are the members' own one-step

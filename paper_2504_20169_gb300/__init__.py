@@ -4,4 +4,4 @@ The compute path is liblbm.so (hand-written sm_103a CUDA behind the C ABI of inc
 this package only marshals arguments to it.
 """
 from ._lib import LBMError, lib  # noqa: F401
-from .solver import Solver, lattice_info  # noqa: F401
+from .solver import Solver, estimate_bytes, lattice_info, peak_fma  # noqa: F401

@@ -62,6 +62,13 @@ PROTOTYPES = {
     "lbm_profile_read": (C.c_int, [_ctx, _dp, C.POINTER(C.c_int)]),
     "lbm_estimate_bytes": (C.c_int, [C.POINTER(lbm_grid), C.c_int, C.c_int, C.c_int, C.c_int,
                                      C.POINTER(C.c_size_t)]),
+    "lbm_estimate_bytes_bc": (C.c_int, [C.POINTER(lbm_grid), C.c_int, C.c_int,
+                                        C.POINTER(lbm_sigma_profile), C.c_int,
+                                        C.POINTER(lbm_bc_params), C.c_int,
+                                        C.POINTER(C.c_size_t)]),
+    "lbm_export_pull_index": (C.c_int, [_ctx, C.c_void_p]),
+    "lbm_export_site_class": (C.c_int, [_ctx, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_peak_fma": (C.c_int, [C.c_int, _dp, _dp, C.c_void_p]),
     "lbm_batch_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "lbm_batch_set": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
     "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int]),

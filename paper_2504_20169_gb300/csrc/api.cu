@@ -354,11 +354,12 @@ extern "C" lbm_status lbm_estimate_bytes(const lbm_grid* grid, lbm_stencil stenc
   return LBM_OK;
 }
 
-lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int pml_width,
-                      const lbm_sigma_profile* sigma, lbm_bc_kind bc, const lbm_bc_params* bcp,
-                      lbm_precision precision, void* cuda_stream, lbm_ctx** out) {
-  if (!out) return LBM_EINVAL;
-  *out = nullptr;
+// Argument checks of lbm_create (shared with lbm_estimate_bytes_bc): the resolved sigma
+// profile, boundary parameters and per-edge PML widths, or LBM_EINVAL with the reason.
+static lbm_status check_args(const lbm_grid* grid, lbm_stencil stencil, double tau, int pml_width,
+                             const lbm_sigma_profile* sigma, lbm_bc_kind bc,
+                             const lbm_bc_params* bcp, lbm_precision precision,
+                             lbm_sigma_profile& sg, lbm_bc_params& bp, int W4[4]) {
   auto fail = [](const char* m) { g_create_error = m; return LBM_EINVAL; };
   if (!grid) return fail("grid is NULL");
   const int q = (int)stencil;
@@ -369,16 +370,14 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
     return fail("pml_width must be 0 or 2..4096");
   if (bc != LBM_BC_PERIODIC && bc != LBM_BC_ZG && bc != LBM_BC_NRBC) return fail("bad bc kind");
   if (precision != LBM_FP64 && precision != LBM_FP32_DEV) return fail("bad precision");
-  lbm_sigma_profile sg = sigma ? *sigma : lbm_sigma_profile{0.0, 2, 0};
+  sg = sigma ? *sigma : lbm_sigma_profile{0.0, 2, 0};
   if (!(sg.sigma_max >= 0.0) || !std::isfinite(sg.sigma_max) || sg.power < 0 || sg.power > 16 ||
       (sg.split != 0 && sg.split != 1))
     return fail("bad sigma profile");
-  lbm_bc_params bp;
   if (bcp) bp = *bcp;
   else { std::memset(&bp, 0, sizeof bp); bp.rho0 = 1.0; bp.T0 = 1.0; }
   if (bp.periodic_y != 0 && bp.periodic_y != 1) return fail("periodic_y must be 0 or 1");
   if (bp.use_pml_widths != 0 && bp.use_pml_widths != 1) return fail("use_pml_widths must be 0 or 1");
-  int W4[4];
   for (int k = 0; k < 4; ++k) W4[k] = bp.use_pml_widths ? bp.pml_widths[k] : pml_width;
   if (bp.periodic_y && !bp.use_pml_widths) W4[2] = W4[3] = 0;
   for (int k = 0; k < 4; ++k)
@@ -398,6 +397,41 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   if (bp.relax_sign != 0.0 && bp.relax_sign != 1.0 && bp.relax_sign != -1.0)
     return fail("relax_sign must be -1, +1 or 0");
   if ((long long)grid->nx * grid->ny > (1ll << 31) / 2) return fail("grid too large");
+  return LBM_OK;
+}
+
+lbm_status lbm_estimate_bytes_bc(const lbm_grid* grid, lbm_stencil stencil, int pml_width,
+                                 const lbm_sigma_profile* sigma, lbm_bc_kind bc,
+                                 const lbm_bc_params* bc_params, lbm_precision precision,
+                                 size_t* bytes) {
+  if (!bytes) return LBM_EINVAL;
+  lbm_sigma_profile sg;
+  lbm_bc_params bp;
+  int W4[4];
+  const lbm_status st = check_args(grid, stencil, 0.75, pml_width, sigma, bc, bc_params,
+                                   precision, sg, bp, W4);
+  if (st != LBM_OK) return st;
+  const int q = (int)stencil;
+  const Geom g = make_geom(grid->nx, grid->ny, W4, halo_of(q), bp.periodic_y, bp.pml_grad);
+  *bytes = bytes_of(g, q, precision == LBM_FP64 ? 8 : 4);
+  return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int pml_width,
+                      const lbm_sigma_profile* sigma, lbm_bc_kind bc, const lbm_bc_params* bcp,
+                      lbm_precision precision, void* cuda_stream, lbm_ctx** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  auto fail = [](const char* m) { g_create_error = m; return LBM_EINVAL; };
+  lbm_sigma_profile sg;
+  lbm_bc_params bp;
+  int W4[4];
+  {
+    const lbm_status st = check_args(grid, stencil, tau, pml_width, sigma, bc, bcp, precision,
+                                     sg, bp, W4);
+    if (st != LBM_OK) return st;
+  }
+  const int q = (int)stencil;
 
   lbm_ctx* ctx = new lbm_ctx();
   if (const char* b = std::getenv("LBM_DEBUG_ALLOC_BUDGET")) ctx->alloc_budget = std::strtoull(b, nullptr, 10);
@@ -761,6 +795,90 @@ lbm_status lbm_import_populations(lbm_ctx* ctx, const double* host) {
   cudaFree(tmp);
   LBM_CK(e);
   ctx->prev_valid = false;
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+// Diagnostic exports: the index maps and the site classification as the kernels compute them.
+namespace lbm {
+template <class S>
+__global__ void k_pull_index(Geom g, long long* __restrict__ out) {
+  const long long nf = (long long)g.Lx * g.Ly, n = (long long)S::Q * nf;
+  const int Gx = g.Lx + 2 * g.M;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = int(t / nf);
+    const long long k = t - (long long)i * nf;
+    const int y = int(k / g.Lx), x = int(k - (long long)y * g.Lx);
+    const long long src = pull_src(g, gindex(g, x, y), S::ex(i), S::ey(i));
+    const long long row = src / g.pitch, col = src - row * g.pitch;
+    out[t] = row * Gx + (col - g.cF0 + g.M);   // G coordinates (gy, gx), row-major
+  }
+}
+
+__global__ void k_site_class(Geom g, Consts<double> c, int* __restrict__ layer,
+                             unsigned char* __restrict__ hasq, double* __restrict__ sxo,
+                             double* __restrict__ syo) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= g.Lx) return;
+  const PmlNode<double> n = pml_node<double>(g, x, y);
+  const long long k = (long long)y * g.Lx + x;
+  layer[k] = max(n.ix, n.iy);
+  hasq[k] = has_pml(g) && n.has_q ? 1 : 0;
+  double sx = 0.0, sy = 0.0;
+  if (n.in_p) pml_sigmas(c, n, sx, sy);
+  sxo[k] = sx;
+  syo[k] = sy;
+}
+}  // namespace lbm
+
+extern "C" {
+
+lbm_status lbm_export_pull_index(lbm_ctx* ctx, int64_t* host) {
+  if (!ctx) return LBM_EINVAL;
+  if (!host) { ctx->err = "NULL output"; return LBM_EINVAL; }
+  LBM_CK(cudaSetDevice(ctx->device));
+  const Geom& g = ctx->g;
+  const size_t n = (size_t)ctx->q * g.Lx * g.Ly;
+  long long* tmp = nullptr;
+  LBM_CK(cudaMalloc(&tmp, n * sizeof(long long)));
+  if (ctx->q == 37) k_pull_index<D2Q37><<<512, 256, 0, ctx->st>>>(g, tmp);
+  else if (ctx->q == 17) k_pull_index<D2Q17><<<512, 256, 0, ctx->st>>>(g, tmp);
+  else k_pull_index<D2Q9><<<512, 256, 0, ctx->st>>>(g, tmp);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, tmp, n * sizeof(long long), cudaMemcpyDeviceToHost, ctx->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  cudaFree(tmp);
+  LBM_CK(e);
+  return LBM_OK;
+}
+
+lbm_status lbm_export_site_class(lbm_ctx* ctx, int32_t* layer, uint8_t* has_q, double* sigma_x,
+                                 double* sigma_y) {
+  if (!ctx) return LBM_EINVAL;
+  LBM_CK(cudaSetDevice(ctx->device));
+  const Geom& g = ctx->g;
+  const size_t n = (size_t)g.Lx * g.Ly;
+  char* tmp = nullptr;
+  const size_t bytes = n * (sizeof(int) + 1 + 2 * sizeof(double)) + 64;
+  LBM_CK(cudaMalloc(&tmp, bytes));
+  double* sx = reinterpret_cast<double*>(tmp);
+  double* sy = sx + n;
+  int* ly = reinterpret_cast<int*>(sy + n);
+  unsigned char* hq = reinterpret_cast<unsigned char*>(ly + n);
+  k_site_class<<<dim3((g.Lx + 127) / 128, g.Ly), 128, 0, ctx->st>>>(g, ctx->dev.cd, ly, hq, sx, sy);
+  cudaError_t e = cudaGetLastError();
+  auto get = [&](void* dst, const void* src, size_t b) {
+    if (dst && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, ctx->st);
+  };
+  get(layer, ly, n * sizeof(int));
+  get(has_q, hq, n);
+  get(sigma_x, sx, n * sizeof(double));
+  get(sigma_y, sy, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  cudaFree(tmp);
+  LBM_CK(e);
   return LBM_OK;
 }
 

@@ -89,6 +89,7 @@ __device__ inline int dist_out(const Geom& g, int x, int y) {
 template <class Real>
 struct PmlNode {
   bool has_q, in_p;
+  int ix, iy;        // layer index along x and along y (0 outside that axis' slabs)
   Real fx, fy;
 };
 
@@ -99,6 +100,8 @@ __device__ inline PmlNode<Real> pml_node(const Geom& g, int x, int y) {
   const int is = g.Ws > 0 ? max(0, g.Ws - y) : 0, in = g.Wn > 0 ? max(0, g.Wn - ey) : 0;
   PmlNode<Real> n;
   n.in_p = (iw | ie | is | in) > 0;
+  n.ix = iw + ie;
+  n.iy = is + in;
   const int r = g.qr - 1;
   n.has_q = (g.Ww > 0 && x <= g.Ww + r) || (g.We > 0 && ex <= g.We + r) ||
             (g.Ws > 0 && y <= g.Ws + r) || (g.Wn > 0 && ey <= g.Wn + r);
@@ -322,12 +325,17 @@ __device__ inline bool unphysical(const Macro<Real>& m) {
   return !(m.rho > Real(0)) || !(T > Real(0)) || !(m.rho < Real(1e30)) || !(T < Real(1e30));
 }
 
+// Storage index of the pull source x - e_i of the node at storage index idx (Eq. lbe).
+__host__ __device__ inline long long pull_src(const Geom& g, long long idx, int ex, int ey) {
+  return idx - (long long)ey * g.pitch - ex;
+}
+
 template <class S, class Real, bool STREAM>
 __device__ inline void load_pop(Real (&p)[S::Q], const Real* __restrict__ A, const Geom& g,
                                 long long idx) {
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) {
-    const long long src = STREAM ? idx - (long long)S::ey(i) * g.pitch - S::ex(i) : idx;
+    const long long src = STREAM ? pull_src(g, idx, S::ex(i), S::ey(i)) : idx;
     p[i] = __ldg(A + (long long)i * g.plane + src);
   }
 }

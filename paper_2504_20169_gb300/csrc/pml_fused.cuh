@@ -183,9 +183,7 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
   else if (!g.py && y == g.Ly - 1) {
     cy0 = 1.5f; cy1 = -2.f; cy2 = 0.5f; oy0 = 0; oy1 = -ew; oy2 = -2 * ew;
   }
-  // Appendix PML source at the outermost layer: moments of the selected parts of Omega^PML
-  const bool src = src_mask && outermost(g, x, y);
-  double smom[4] = {0.0, 0.0, 0.0, 0.0};   // FP64 sums (cancellation)
+  // the hot loop: BGK + PML term, S^n, store
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) {
     const float eq = eq_dir<S, float, true>(i, m, kc, c);
@@ -199,19 +197,28 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
       if (S::ex(i) != 0) gq += sy * float(S::ex(i)) * (cx0 * q[ox0] + cx1 * q[ox1] + cx2 * q[ox2]);
       if (S::ey(i) != 0) gq += sx * float(S::ey(i)) * (cy0 * q[oy0] + cy1 * q[oy1] + cy2 * q[oy2]);
       out = out - (gq + ssum * fhat + sprod * qn);
-      if (src) {
-        const double part = -(((src_mask & 1) ? double(gq) : 0.0) +
-                              ((src_mask & 2) ? double(ssum) * double(fhat) : 0.0) +
-                              ((src_mask & 4) ? double(sprod) * double(qn) : 0.0));
-        smom[0] += part;
-        smom[1] += double(S::ex(i)) * part;
-        smom[2] += double(S::ey(i)) * part;
-        smom[3] += double(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
-      }
     }
     B[(long long)i * g.plane + idx] = out;
   }
-  if (src) {
+  // Appendix PML source at the outermost layer (a small fraction of the frame): the moments
+  // of the selected parts of Omega^PML, recomputed term by term and summed in FP64 (the sums
+  // cancel heavily), outside the hot loop so that it keeps its registers
+  if (src_mask && in_p && outermost(g, x, y)) {
+    double smom[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < S::Q; ++i) {
+      const float fhat = eq_dir<S, float, true>(i, m, kc, c) - c.eqbar[i];
+      const float* q = Qs + i * next + e0;
+      float gq = 0.f;
+      if (S::ex(i) != 0) gq += sy * float(S::ex(i)) * (cx0 * q[ox0] + cx1 * q[ox1] + cx2 * q[ox2]);
+      if (S::ey(i) != 0) gq += sx * float(S::ey(i)) * (cy0 * q[oy0] + cy1 * q[oy1] + cy2 * q[oy2]);
+      const double part = -(((src_mask & 1) ? double(gq) : 0.0) +
+                            ((src_mask & 2) ? double(ssum) * double(fhat) : 0.0) +
+                            ((src_mask & 4) ? double(sprod) * double(q[0]) : 0.0));
+      smom[0] += part;
+      smom[1] += double(S::ex(i)) * part;
+      smom[2] += double(S::ey(i)) * part;
+      smom[3] += double(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
+    }
     smom[1] *= double(c.r);
     smom[2] *= double(c.r);
     smom[3] *= 0.5 * double(c.r2);

@@ -170,6 +170,23 @@ class Solver:
         buf = C.create_string_buffer(data, len(data))
         _check(L.lib().lbm_restore(self.ctx, buf, len(data)), self.ctx)
 
+    def pull_index(self):
+        """(q, Ly, Lx) int64: G index gy * (Lx + 2M) + gx of every pull source x - e_i."""
+        out = np.empty((self.q, self.Ly, self.Lx), dtype=np.int64)
+        _check(L.lib().lbm_export_pull_index(self.ctx, out.ctypes.data_as(C.c_void_p)), self.ctx)
+        return out
+
+    def site_class(self):
+        """(layer index, has_q, sigma_x, sigma_y) per node of F, each (Ly, Lx)."""
+        shp = (self.Ly, self.Lx)
+        layer = np.empty(shp, dtype=np.int32)
+        hq = np.empty(shp, dtype=np.uint8)
+        sx, sy = np.empty(shp), np.empty(shp)
+        _check(L.lib().lbm_export_site_class(self.ctx, *[a.ctypes.data_as(C.c_void_p)
+                                                         for a in (layer, hq, sx, sy)]),
+               self.ctx)
+        return layer, hq.astype(bool), sx, sy
+
     KERNEL_CLASSES = ("targets", "interior", "frame1", "frame2", "band")
 
     def profile_enable(self, max_steps):
@@ -193,3 +210,30 @@ class Solver:
         g = (C.c_int64 * 12)()
         _check(L.lib().lbm_geometry(self.ctx, g), self.ctx)
         return int(g[7])
+
+
+def estimate_bytes(nx, ny, W, q=37, bc="zg", precision="fp32dev", pml_widths=None,
+                   periodic_y=False, pml_grad="central", sigma_split=False):
+    """Device bytes lbm_create would allocate (lbm_estimate_bytes_bc; host only)."""
+    grid = L.lbm_grid(nx, ny)
+    sig = L.lbm_sigma_profile(0.1, 2, 1 if sigma_split else 0)
+    bp = L.lbm_bc_params()
+    bp.rho0, bp.T0 = 1.0, 1.0
+    if pml_widths is not None:
+        bp.use_pml_widths = 1
+        for k in range(4):
+            bp.pml_widths[k] = int(pml_widths[k])
+    bp.periodic_y = 1 if periodic_y else 0
+    bp.pml_grad = {"central": 0, "link": 1}[pml_grad]
+    n = C.c_size_t()
+    _check(L.lib().lbm_estimate_bytes_bc(C.byref(grid), q, int(W), C.byref(sig), _BC[bc],
+                                         C.byref(bp), _PREC[precision], C.byref(n)))
+    return n.value
+
+
+def peak_fma(precision="fp64", stream=None):
+    """Measured FMA throughput of the current device in TFLOP/s (lbm_peak_fma)."""
+    t, ms = C.c_double(), C.c_double()
+    _check(L.lib().lbm_peak_fma(_PREC[precision], C.byref(t), C.byref(ms),
+                                C.c_void_p(stream.cuda_stream if stream is not None else 0)))
+    return t.value, ms.value

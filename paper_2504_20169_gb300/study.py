@@ -123,7 +123,7 @@ def step_cases(q):
 
 
 def run_density_step(q=37, Lx=200, Ly=20, steps=2000, sample=20, tau=0.8, Ma=0.05,
-                     precision="fp64", prof_steps=100, cases=None):
+                     precision="fp64", prof_steps=100, cases=None, pml_grad="central"):
     import torch
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import workloads as wl
@@ -144,7 +144,7 @@ def run_density_step(q=37, Lx=200, Ly=20, steps=2000, sample=20, tau=0.8, Ma=0.0
     mean = (1.0, Ma, 0.0, 1.0)
     for label, bc, W, sig, src in (cases if cases is not None else step_cases(q)):
         s = Solver(Lx, Ly, W, tau, sig, 2, bc, q, (0, 0, 0, 0), 0.0, mean,
-                   precision=precision, periodic_y=True, pml_source=src)
+                   precision=precision, periodic_y=True, pml_source=src, pml_grad=pml_grad)
         fields = wl.density_step(Lx, Ly, Ma=Ma, W=W, Wy=0)
         s.init(*fields)
         e = {"rho": [], "ux": []}
@@ -175,7 +175,7 @@ def run_density_step(q=37, Lx=200, Ly=20, steps=2000, sample=20, tau=0.8, Ma=0.0
                          if r_["ebar"][k] and base["ebar"][k] else None) for k in r_["ebar"]}
         r_["C_t"] = r_["t_bc_us"] / base["t_bc_us"]
     meta = {"case": "density_step", "Lx": Lx, "Ly": Ly, "steps": steps, "sample": sample,
-            "tau": tau, "Ma": Ma, "q": q, "precision": precision,
+            "tau": tau, "Ma": Ma, "q": q, "precision": precision, "pml_grad": pml_grad,
             "reference_grid": [Lx + 2 * pad, Ly]}
     return meta, results
 
@@ -230,6 +230,44 @@ def run_bench_workload(steps=200, sample=20, precision="fp32dev", n=2048, W=32):
     return meta, results
 
 
+def run_stability_map(N=256, steps=10000, chunk=500, precision="fp64"):
+    """How long each boundary treatment survives (section "long runs" of the design notes):
+    isentropic vortex R 20, Mv 0.05 on an N^2 bulk, PML W 32 with cubic sigma_max 0.1 where a
+    PML is used, D2Q37 and D2Q17, tau 0.55 / 0.8, mean flow Mach 0 / 0.3; periodic, ZG,
+    PNR-LODI and east CBC relax without PML, and ZG / PNR / east CBC relax with the printed
+    and with the link-integrated PML gradient. Each run is checked every `chunk` steps through
+    the library's unphysical-state flag."""
+    import workloads as wl
+    from . import LBMError, Solver
+    out = []
+    for q in (37, 17):
+        for tau in (0.55, 0.8):
+            for Ma in (0.0, 0.3):
+                runs = [(0, "periodic", (0, 0, 0, 0), "central")]
+                for W in (0, 32):
+                    for bc, edges in (("zg", (0, 0, 0, 0)), ("nrbc", (0, 0, 0, 0)),
+                                      ("nrbc", (0, 1, 0, 0))):
+                        for grad in (("central",) if W == 0 else ("central", "link")):
+                            runs.append((W, bc, edges, grad))
+                for W, bc, edges, grad in runs:
+                    f = wl.isentropic_vortex(N, N, W, R=20.0, Mv=0.05, mean_u=(Ma, 0.0))
+                    s = Solver(N, N, W, tau, 0.1 if W else 0.0, 3, bc, q, edges, Ma,
+                               (1.0, Ma, 0.0, 1.0), precision=precision, pml_grad=grad)
+                    s.init(*f)
+                    done, status = 0, "ok"
+                    try:
+                        while done < steps:
+                            s.step(chunk)
+                            s.sync()
+                            done += chunk
+                    except LBMError:
+                        status = f"div. {done + chunk}"
+                    s.close()
+                    out.append(dict(q=q, tau=tau, Ma=Ma, W=W, bc=bc, edges=list(edges),
+                                    grad=grad, status=status))
+    return out
+
+
 def _fmt(v):
     return "n/a" if v is None else f"{v:.3g}"
 
@@ -237,8 +275,11 @@ def _fmt(v):
 def main():
     import argparse
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="all", choices=("vortex", "step", "scan", "bench", "all"))
+    ap.add_argument("--case", default="all", choices=("vortex", "step", "scan", "bench", "stability", "all"))
     ap.add_argument("--tau", type=float, default=0.8)
+    ap.add_argument("--grad", default="central", choices=("central", "link"),
+                    help="PML gradient of the density-step cases: the printed central "
+                         "differences or the link-integrated option")
     ap.add_argument("--steps", type=int, default=None)
     a = ap.parse_args()
     if a.case in ("bench", "all"):
@@ -262,7 +303,8 @@ def main():
         for q in (9, 17, 37):
             cases = [("ZG", "zg", 0, 0.0, 0)] + [("ZG", "zg", 20, v, 0) for v in sig] + \
                     [("LODI", "nrbc", 20, v, 0) for v in sig]
-            meta, results = run_density_step(q=q, steps=a.steps or 2000, tau=a.tau, cases=cases)
+            meta, results = run_density_step(q=q, steps=a.steps or 2000, tau=a.tau, cases=cases,
+                                             pml_grad=a.grad)
             print(json.dumps(meta))
             for r in results:
                 eb, cz = r["ebar"], r["C_Z"]
@@ -273,7 +315,8 @@ def main():
         print("| q | BC | W | sigma_max | e_bar rho | e_bar u_x | max e rho | C_rho | C_ux | C_t |")
         print("|---|---|---|---|---|---|---|---|---|---|")
         for q in (9, 17, 37):
-            meta, results = run_density_step(q=q, steps=a.steps or 2000, tau=a.tau)
+            meta, results = run_density_step(q=q, steps=a.steps or 2000, tau=a.tau,
+                                             pml_grad=a.grad)
             print(json.dumps(meta))
             for r in results:
                 print(json.dumps(r))
@@ -283,6 +326,9 @@ def main():
                       f"{_fmt(eb['ux'])} | {_fmt(r['emax']['rho'])} | {_fmt(cz['rho'])} | "
                       f"{_fmt(cz['ux'])} | {r['C_t']:.1f} |"
                       + ("" if r["status"] == "ok" else f" {r['status']}"))
+    if a.case == "stability":
+        for r in run_stability_map(steps=a.steps or 10000):
+            print(json.dumps(r))
     if a.case in ("vortex", "all"):
         meta, results = run(steps=a.steps or 1500, tau=a.tau)
         print(json.dumps(meta))

@@ -103,3 +103,45 @@ def test_null_safety(L):
     assert lib.lbm_destroy(None) == L.LBM_OK
     assert lib.lbm_step(None, 1) == L.LBM_EINVAL
     assert lib.lbm_geometry(None, None) == L.LBM_EINVAL
+
+
+def test_estimate_bytes_bc_follows_the_grid_shape(L):
+    """lbm_estimate_bytes_bc (host only) budgets per-edge widths, the periodic y axis and the
+    link gradient's wider accumulator; with equal widths it equals lbm_estimate_bytes."""
+    from paper_2504_20169_gb300 import estimate_bytes
+    grid = L.lbm_grid(256, 256)
+    n = C.c_size_t()
+    assert L.lib().lbm_estimate_bytes(C.byref(grid), 37, 32, L.LBM_BC_NRBC, L.LBM_FP32_DEV,
+                                      C.byref(n)) == L.LBM_OK
+    base = estimate_bytes(256, 256, 32, bc="nrbc")
+    assert base == n.value
+    thin = estimate_bytes(256, 256, 32, bc="nrbc", pml_widths=(8, 32, 8, 8))
+    py = estimate_bytes(256, 256, 32, bc="nrbc", periodic_y=True)
+    link = estimate_bytes(256, 256, 32, bc="nrbc", pml_grad="link")
+    assert thin < base and py < base and link > base
+    # FP64 holds twice the populations
+    assert estimate_bytes(256, 256, 32, bc="nrbc", precision="fp64") > 1.9 * base
+
+
+@pytest.mark.parametrize("kw", [dict(pml_grad="link", sigma_split=True),
+                                dict(pml_widths=(1, 4, 4, 4)), dict(bc="periodic")])
+def test_estimate_bytes_bc_rejects_what_create_rejects(L, kw):
+    from paper_2504_20169_gb300 import LBMError, estimate_bytes
+    with pytest.raises(LBMError):
+        estimate_bytes(64, 64, 8, **kw)
+
+
+def test_link_gradient_needs_equal_sigmas(L):
+    grid = L.lbm_grid(32, 32)
+    sig = L.lbm_sigma_profile(0.1, 3, 1)
+    bp = L.lbm_bc_params()
+    bp.rho0, bp.T0, bp.pml_grad = 1.0, 1.0, 1
+    out = C.c_void_p(123)
+    st = L.lib().lbm_create(C.byref(grid), 37, 0.8, 4, C.byref(sig), L.LBM_BC_ZG, C.byref(bp),
+                            L.LBM_FP64, None, C.byref(out))
+    assert st == L.LBM_EINVAL and out.value is None
+    bp.pml_grad = 2
+    sig.split = 0
+    st = L.lib().lbm_create(C.byref(grid), 37, 0.8, 4, C.byref(sig), L.LBM_BC_ZG, C.byref(bp),
+                            L.LBM_FP64, None, C.byref(out))
+    assert st == L.LBM_EINVAL
