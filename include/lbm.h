@@ -235,19 +235,33 @@ lbm_status lbm_export_site_class(lbm_ctx* ctx, int32_t* layer, uint8_t* has_q, d
 lbm_status lbm_peak_fma(lbm_precision precision, double* tflops, double* ms, void* cuda_stream);
 
 /* Batched execution of independent instances (serving). A batch holds a resident set of
- * initialized contexts on one device and advances all of them together: each step is one
- * CUDA-graph launch on the batch's stream whose child graphs are the members' own one-step
- * graphs, so instances of different sizes, PML widths and boundary conditions overlap on the
- * GPU while every member computes exactly what lbm_step would (bit-identical results).
- * lbm_batch_set replaces the resident set (continuous batching: call it between steps as
- * instances are admitted or retired; the combined graph is rebuilt on the next step).
+ * initialized contexts on one device and advances all of them together. Members are grouped
+ * by (stencil, precision, PML gradient mode); within a group every kernel class (characteristic
+ * targets, interior, PML frame, boundary band, periodic row copies) is one launch whose blocks
+ * walk a table of (member, tile) entries spanning all members of the group, so instances of
+ * different sizes, PML widths and boundary conditions share each launch and fill the GPU
+ * together; one step of the whole batch is one CUDA-graph launch on the batch's stream. Each
+ * block runs the same per-node code as lbm_step, so every member computes bit for bit what it
+ * computes alone, whatever the tile shape. lbm_batch_set replaces the resident set (continuous
+ * batching: call it between steps as instances are admitted or retired; the plans and graphs are
+ * rebuilt on the next step, as they are when a member was stepped on its own in between).
  * lbm_batch_step returns LBM_EUNSTABLE without stepping anyone if a member has flagged an
  * unphysical state (find it with lbm_sync, drop it with lbm_batch_set). The batch does not own
- * its members; destroy a context only after removing it from every batch. */
+ * its members; destroy a context only after removing it from every batch.
+ * lbm_batch_tile sets the interior kernel's block shape tx x by (tx in {32, 64, 128, 256},
+ * by >= 1, tx * by <= 256; 0, 0 = the tuned shape for this stencil, precision and device if
+ * one was found in this process, else 32 x 4). lbm_batch_autotune times `steps` batch steps
+ * with each of the candidate shapes 32x2, 32x4, 32x8, 64x2, 64x4, 128x1, 128x2, 256x1 (one
+ * untimed step each to build them), keeps the fastest for this batch, records it for
+ * (stencil, precision, PML gradient mode, device name) for later batches of the process, and
+ * returns it in *tx, *by (either may be NULL). Tuning steps are real steps: every member
+ * advances by 8 (steps + 1); the shape never changes the results. */
 typedef struct lbm_batch lbm_batch;
 lbm_status lbm_batch_create(void* cuda_stream, lbm_batch** out);
 lbm_status lbm_batch_set(lbm_batch* batch, lbm_ctx* const* ctxs, int count);
 lbm_status lbm_batch_step(lbm_batch* batch, int n);
+lbm_status lbm_batch_tile(lbm_batch* batch, int tx, int by);
+lbm_status lbm_batch_autotune(lbm_batch* batch, int steps, int* tx, int* by);
 lbm_status lbm_batch_destroy(lbm_batch* batch);
 
 /* Conserved totals of macroscopic fields that the caller already holds on the device, computed
@@ -263,7 +277,9 @@ lbm_status lbm_batch_destroy(lbm_batch* batch);
  * call on a device shares it and rewrites all the slots it uses, so nothing needs clearing, but
  * calls that overlap on the GPU (other streams, other threads) race on it. The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that device current:
- * make that first call before any stream capture. No cudaMalloc, cudaFree or allocating library
+ * make that first call before any stream capture. The looked-up address is kept for the life of
+ * the process, so do not call this after cudaDeviceReset of that device (the module, and with it
+ * the array, may then sit elsewhere). No cudaMalloc, cudaFree or allocating library
  * routine is called. Asynchronous on cuda_stream (a cudaStream_t, NULL = legacy default stream).
  * Errors are reported by lbm_last_error(NULL). */
 #define LBM_TOTALS_NOALLOC_MAX_N ((int64_t)1 << 28)

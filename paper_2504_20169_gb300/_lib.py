@@ -73,6 +73,9 @@ PROTOTYPES = {
     "lbm_batch_set": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
     "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_batch_tile": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "lbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int),
+                                     C.POINTER(C.c_int)]),
     "lbm_totals_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                      C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [_ctx]),

@@ -1,6 +1,7 @@
 // C ABI of liblbm (include/lbm.h): context management, validation, the quadrature of Sec. 2,
 // and the host-side sequencing of the kernels.
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -199,6 +200,7 @@ struct lbm_ctx {
   std::vector<cudaEvent_t> prof;   // kKernelClasses * 2 events per recorded step
   int prof_cap = 0, prof_used = 0;
   // device buffers: base pointer (guard band of kGuard bytes on both sides) and payload size
+  BatchPlan plan{};           // one-member plan: the table-driven boundary-side launches
   std::vector<std::pair<char*, size_t>> allocs;
   size_t alloc_total = 0, alloc_budget = 0;  // budget 0: unlimited (test hook, see lbm.h)
   std::string err;
@@ -250,6 +252,7 @@ static void free_all(lbm_ctx* ctx) {
   if (ctx->join) cudaEventDestroy(ctx->join);
   if (ctx->join2) cudaEventDestroy(ctx->join2);
   if (ctx->ready) cudaEventDestroy(ctx->ready);
+  batch_plan_free(&ctx->plan);
   for (auto& a : ctx->allocs) cudaFree(a.first);
   ctx->allocs.clear();
   if (ctx->hout) cudaFreeHost(ctx->hout);
@@ -261,6 +264,7 @@ static size_t source_slots(const Geom& g) { return 4 * 2 * ((size_t)g.Lx + g.Ly)
 
 static void set_roles(lbm_ctx* ctx, int a, int s) {
   Dev& d = ctx->dev;
+  d.which = a;
   d.A = ctx->f[a];
   d.B = ctx->f[1 - a];
   d.Sold = ctx->S[s];
@@ -549,6 +553,17 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   d.cf.r = (float)ctx->r; d.cf.r2 = (float)(ctx->r * ctx->r); d.cf.omega = (float)ctx->omega;
   d.cf.sigma_max = (float)sg.sigma_max; d.cf.power = sg.power; d.cf.split = sg.split;
   if (ctx->ops.prepare() != cudaSuccess) return oom("kernel attributes");
+  {
+    // the context's one-member plan, for buffer parity 0 and 1
+    set_roles(ctx, 0, 0);
+    Dev d0 = ctx->dev;
+    set_roles(ctx, 1, 1);
+    Dev d1 = ctx->dev;
+    const Dev* p0 = &d0;
+    const Dev* p1 = &d1;
+    if (ctx->ops.batch_plan(&p0, &p1, 1, 32, 4, &ctx->plan) != cudaSuccess) return oom("plan");
+    ctx->dev.plan = &ctx->plan;
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) return oom("device sync");
   *out = ctx;
   return LBM_OK;
@@ -996,37 +1011,157 @@ lbm_status lbm_restore(lbm_ctx* ctx, const void* host, size_t bytes) {
 }  // extern "C"
 
 // --------------------------------------------------------------------------------------------
-// Batched execution: one combined graph per step over the resident set (see lbm.h).
+// Batched execution (see lbm.h): the members are grouped by (stencil, precision, PML gradient
+// mode); each group is one plan whose kernels each cover every member of the group in one
+// launch (a table of (member, tile) entries), and one step of all groups is one captured graph
+// per buffer-parity state.
+#include <map>
+#include <tuple>
+
+namespace {
+struct BatchGroup {
+  OpsTable ops;
+  std::vector<int> idx;     // member indices
+  BatchPlan plan;
+};
+// autotuned bulk tile shape per (stencil, precision, PML gradient mode, device name)
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, std::string>, std::pair<int, int>> g_tune_cache;
+
+std::string device_name(int dev) {
+  cudaDeviceProp pr;
+  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "?";
+  return pr.name;
+}
+}  // namespace
+
 struct lbm_batch {
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;              // the caller's stream
+  cudaStream_t cap = nullptr, aux = nullptr, aux2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
+  int device = -1;
   std::vector<lbm_ctx*> members;
-  // combined executable graphs keyed by the members' buffer parities at launch time
-  std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> cache;
+  std::vector<int> base;                  // members' buffer parity when the plans were built
+  std::vector<BatchGroup> groups;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int tx = 0, by = 0;                     // bulk tile shape; 0: from the tuning cache / default
+  bool built = false;
   std::string err;
 };
 
 static void batch_clear(lbm_batch* b) {
-  for (auto& e : b->cache) cudaGraphExecDestroy(e.second);
-  b->cache.clear();
+  for (int k = 0; k < 2; ++k)
+    if (b->graph[k]) { cudaGraphExecDestroy(b->graph[k]); b->graph[k] = nullptr; }
+  for (auto& g : b->groups) batch_plan_free(&g.plan);
+  b->groups.clear();
+  b->built = false;
+}
+
+void lbm::batch_plan_free(BatchPlan* p) {
+  if (p->mem) cudaFree(p->mem);
+  *p = BatchPlan();
+}
+
+static std::tuple<int, int, int, std::string> tune_key(const lbm_ctx* c) {
+  return {c->q, (int)c->prec, c->g.link, device_name(c->device)};
+}
+
+// Plans and the two step graphs for the current member set and tile shape.
+static lbm_status batch_build(lbm_batch* b) {
+  batch_clear(b);
+  if (b->members.empty()) return LBM_OK;
+  lbm_ctx* ctx = b->members[0];   // for LBM_CK messages
+  LBM_CK(cudaSetDevice(b->device));
+  int tx = b->tx, by = b->by;
+  if (!tx) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(tune_key(ctx));
+    tx = it != g_tune_cache.end() ? it->second.first : 32;
+    by = it != g_tune_cache.end() ? it->second.second : 4;
+  }
+  std::map<std::tuple<int, int, int>, int> gi;
+  for (int m = 0; m < (int)b->members.size(); ++m) {
+    lbm_ctx* c = b->members[m];
+    auto key = std::make_tuple(c->q, (int)c->prec, c->g.link);
+    auto it = gi.find(key);
+    if (it == gi.end()) {
+      gi[key] = (int)b->groups.size();
+      b->groups.push_back(BatchGroup{c->ops, {m}, BatchPlan()});
+    } else {
+      b->groups[it->second].idx.push_back(m);
+    }
+  }
+  b->base.resize(b->members.size());
+  for (auto& G : b->groups) {
+    std::vector<Dev> d0, d1;
+    for (int m : G.idx) {
+      lbm_ctx* c = b->members[m];
+      b->base[m] = c->cur;
+      set_roles(c, c->cur, c->scur);
+      d0.push_back(c->dev);
+      set_roles(c, c->cur ^ 1, c->scur ^ 1);
+      d1.push_back(c->dev);
+    }
+    std::vector<const Dev*> p0, p1;
+    for (size_t k = 0; k < d0.size(); ++k) { p0.push_back(&d0[k]); p1.push_back(&d1[k]); }
+    const cudaError_t e = G.ops.batch_plan(p0.data(), p1.data(), (int)p0.size(), tx, by, &G.plan);
+    if (e != cudaSuccess) {
+      b->err = std::string("batch plan: ") + cudaGetErrorString(e);
+      batch_clear(b);
+      return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+    }
+  }
+  for (int w = 0; w < 2; ++w) {
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      for (auto& G : b->groups)
+        if (e == cudaSuccess)
+          e = G.ops.batch_step(G.plan, w, b->cap, b->aux, b->aux2, b->fork, b->join, b->join2);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph[w], graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+    }
+    if (e != cudaSuccess) {
+      b->err = std::string("batch graph: ") + cudaGetErrorString(e);
+      batch_clear(b);
+      return LBM_ECUDA;
+    }
+  }
+  b->built = true;
+  return LBM_OK;
 }
 
 extern "C" {
 
 lbm_status lbm_batch_create(void* cuda_stream, lbm_batch** out) {
   if (!out) return LBM_EINVAL;
+  *out = nullptr;
   lbm_batch* b = new lbm_batch();
   b->st = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&b->device);
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&b->aux, cudaStreamNonBlocking, hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&b->aux2, cudaStreamNonBlocking, hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->join2, cudaEventDisableTiming) != cudaSuccess) {
+    lbm_batch_destroy(b);
+    g_create_error = "lbm_batch_create: stream or event creation failed";
+    return LBM_ECUDA;
+  }
   *out = b;
   return LBM_OK;
 }
 
 lbm_status lbm_batch_set(lbm_batch* b, lbm_ctx* const* ctxs, int count) {
   if (!b || count < 0 || (count > 0 && !ctxs)) return LBM_EINVAL;
-  int dev = -1;
   for (int k = 0; k < count; ++k) {
     if (!ctxs[k] || !ctxs[k]->initialized) { b->err = "batch member not initialized"; return LBM_ESTATE; }
-    if (dev >= 0 && ctxs[k]->device != dev) { b->err = "batch members on different devices"; return LBM_EINVAL; }
-    dev = ctxs[k]->device;
+    if (ctxs[k]->device != b->device) { b->err = "batch member on another device"; return LBM_EINVAL; }
     for (int j = 0; j < k; ++j)
       if (ctxs[j] == ctxs[k]) { b->err = "context listed twice"; return LBM_EINVAL; }
   }
@@ -1036,41 +1171,44 @@ lbm_status lbm_batch_set(lbm_batch* b, lbm_ctx* const* ctxs, int count) {
   return LBM_OK;
 }
 
+lbm_status lbm_batch_tile(lbm_batch* b, int tx, int by) {
+  if (!b) return LBM_EINVAL;
+  if (!((tx == 0 && by == 0) || ((tx == 32 || tx == 64 || tx == 128 || tx == 256) && by >= 1 &&
+                                  tx * by <= 256))) {
+    b->err = "tile: tx in {32, 64, 128, 256}, by >= 1, tx * by <= 256 (or 0, 0)";
+    return LBM_EINVAL;
+  }
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) { b->err = "stream sync failed"; return LBM_ECUDA; }
+  b->tx = tx;
+  b->by = by;
+  batch_clear(b);
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_step(lbm_batch* b, int n) {
   if (!b || n < 0) return LBM_EINVAL;
   if (b->members.empty() || n == 0) return LBM_OK;
   for (lbm_ctx* c : b->members)
     if (*(volatile int*)c->hflag) { b->err = "a member flagged an unphysical state"; return LBM_EUNSTABLE; }
   lbm_ctx* ctx = b->members[0];  // for LBM_CK messages
-  LBM_CK(cudaSetDevice(ctx->device));
+  LBM_CK(cudaSetDevice(b->device));
   for (int k = 0; k < n; ++k) {
-    std::vector<int> key;
-    key.reserve(b->members.size());
-    for (lbm_ctx* c : b->members) key.push_back(c->cur);
-    cudaGraphExec_t exec = nullptr;
-    for (auto& e : b->cache)
-      if (e.first == key) exec = e.second;
-    if (!exec) {
-      for (lbm_ctx* c : b->members)
-        if (!c->gtemplate[c->cur]) {
-          lbm_status gs = build_graph(c, c->cur);
-          if (gs != LBM_OK) { b->err = c->err; return gs; }
-        }
-      cudaGraph_t g = nullptr;
-      LBM_CK(cudaGraphCreate(&g, 0));
-      cudaError_t e = cudaSuccess;
-      for (lbm_ctx* c : b->members) {
-        cudaGraphNode_t node;
-        e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, c->gtemplate[c->cur]);
-        if (e != cudaSuccess) break;
+    // parity state of the members against the plans (a member stepped on its own since
+    // then makes the states disagree: rebuild)
+    int state = -1;
+    if (b->built) {
+      for (size_t m = 0; m < b->members.size(); ++m) {
+        const int s = b->members[m]->cur != b->base[m] ? 1 : 0;
+        if (state < 0) state = s;
+        else if (s != state) { state = -2; break; }
       }
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
-      cudaGraphDestroy(g);
-      LBM_CK(e);
-      if (b->cache.size() >= 4) batch_clear(b);
-      b->cache.emplace_back(key, exec);
     }
-    LBM_CK(cudaGraphLaunch(exec, b->st));
+    if (!b->built || state < 0) {
+      lbm_status bs = batch_build(b);
+      if (bs != LBM_OK) return bs;
+      state = 0;
+    }
+    LBM_CK(cudaGraphLaunch(b->graph[state], b->st));
     for (lbm_ctx* c : b->members) {
       c->cur ^= 1;
       c->scur ^= 1;
@@ -1082,10 +1220,61 @@ lbm_status lbm_batch_step(lbm_batch* b, int n) {
   return LBM_OK;
 }
 
+lbm_status lbm_batch_autotune(lbm_batch* b, int steps, int* tx_out, int* by_out) {
+  if (!b || steps < 1) return LBM_EINVAL;
+  if (b->members.empty()) { b->err = "empty batch"; return LBM_ESTATE; }
+  lbm_ctx* ctx = b->members[0];
+  LBM_CK(cudaSetDevice(b->device));
+  static const int cand[][2] = {{32, 2}, {32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1},
+                                {128, 2}, {256, 1}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LBM_CK(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) { cudaEventDestroy(e0); LBM_CK(ce); }
+  float best = 1e30f;
+  int bt = 32, bb = 4;
+  lbm_status st = LBM_OK;
+  for (const auto& c : cand) {
+    b->tx = c[0];
+    b->by = c[1];
+    batch_clear(b);
+    st = lbm_batch_step(b, 1);   // builds the plan and graphs (one untimed step)
+    if (st != LBM_OK) break;
+    cudaEventRecord(e0, b->st);
+    st = lbm_batch_step(b, steps);
+    if (st != LBM_OK) break;
+    cudaEventRecord(e1, b->st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { st = LBM_ECUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; bt = c[0]; bb = c[1]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->tx = bt;
+  b->by = bb;
+  batch_clear(b);
+  if (st != LBM_OK) return st;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[tune_key(ctx)] = {bt, bb};
+  }
+  if (tx_out) *tx_out = bt;
+  if (by_out) *by_out = bb;
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_destroy(lbm_batch* b) {
   if (!b) return LBM_OK;
+  if (b->device >= 0) cudaSetDevice(b->device);
   cudaStreamSynchronize(b->st);
   batch_clear(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->aux) cudaStreamDestroy(b->aux);
+  if (b->aux2) cudaStreamDestroy(b->aux2);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  if (b->join2) cudaEventDestroy(b->join2);
   delete b;
   return LBM_OK;
 }

@@ -346,12 +346,11 @@ __device__ inline void load_pop(Real (&p)[S::Q], const Real* __restrict__ A, con
 
 // Interior of F (inside the frame depths Fw, Fe, Fs, Fn): pull, moments, BGK, store.
 // Block: 32 x BY threads; the x tiles start on a 32-node boundary of F.
+// (bulk_node is the per-node work, shared with the batched launch over many instances.)
 template <class S, class Real, bool DEV, bool STREAM>
-__global__ void __launch_bounds__(256) k_bulk(Geom g, Consts<Real> c, const Real* __restrict__ A,
-                                              Real* __restrict__ B, int* flag) {
-  const int x0 = (g.Fw / 32) * 32;
-  const int x = x0 + blockIdx.x * 32 + threadIdx.x;
-  const int y = g.Fs + blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void bulk_node(const Geom& g, const Consts<Real>& c,
+                                          const Real* __restrict__ A, Real* __restrict__ B,
+                                          int* flag, int x, int y) {
   if (x < g.Fw || x >= g.Lx - g.Fe || y >= g.Ly - g.Fn) return;
   const long long idx = gindex(g, x, y);
   Real p[S::Q];
@@ -361,6 +360,14 @@ __global__ void __launch_bounds__(256) k_bulk(Geom g, Consts<Real> c, const Real
   collide_bgk<S, Real, DEV>(p, m, c);
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) B[(long long)i * g.plane + idx] = p[i];
+}
+
+template <class S, class Real, bool DEV, bool STREAM>
+__global__ void __launch_bounds__(256) k_bulk(Geom g, Consts<Real> c, const Real* __restrict__ A,
+                                              Real* __restrict__ B, int* flag) {
+  const int x0 = (g.Fw / 32) * 32;
+  bulk_node<S, Real, DEV, STREAM>(g, c, A, B, flag, x0 + blockIdx.x * 32 + threadIdx.x,
+                                  g.Fs + blockIdx.y * blockDim.y + threadIdx.y);
 }
 
 // Writes the time-level moments of a node in the outer two layers of F into every edge slot
@@ -417,11 +424,12 @@ __device__ inline bool outermost(const Geom& g, int x, int y) {
 // the local part -((sigma_x + sigma_y) f_hat + sigma_x sigma_y Q) of Eq. (pml-general)
 // (-sigma (2 f_hat + sigma Q) of Eq. PMLCOLL when sigma_x = sigma_y).
 template <class S, class Real, bool DEV, bool STREAM>
-__global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Real* __restrict__ A,
-                                                Real* __restrict__ B, const Real* __restrict__ Sold,
-                                                Real* __restrict__ Snew, double* Uedge, int save_edges,
-                                                int* flag, double* Sedge, int src_mask) {
-  const int fi = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void frame1_node(const Geom& g, const Consts<Real>& c,
+                                            const Real* __restrict__ A, Real* __restrict__ B,
+                                            const Real* __restrict__ Sold,
+                                            Real* __restrict__ Snew, double* Uedge,
+                                            int save_edges, int* flag, double* Sedge,
+                                            int src_mask, int fi) {
   if (fi >= g.frame_n) return;
   int x, y;
   frame_xy(g, fi, x, y);
@@ -480,15 +488,23 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
   }
 }
 
+template <class S, class Real, bool DEV, bool STREAM>
+__global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Real* __restrict__ A,
+                                                Real* __restrict__ B, const Real* __restrict__ Sold,
+                                                Real* __restrict__ Snew, double* Uedge, int save_edges,
+                                                int* flag, double* Sedge, int src_mask) {
+  frame1_node<S, Real, DEV, STREAM>(g, c, A, B, Sold, Snew, Uedge, save_edges, flag, Sedge,
+                                    src_mask, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Frame, phase 2 (PML nodes): subtract sigma_y c_ix dQ_i/dx + sigma_x c_iy dQ_i/dy (sigma
 // e_i . grad Q_i when sigma_x = sigma_y) with Q = (S^(n-1) + S^n) / 2,
 // Eq. (FD-dx-center) per axis, Eq. (FD-dx-bw) along the outward normal at the outermost layer.
 template <class S, class Real>
-__global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __restrict__ B,
-                                                const Real* __restrict__ Sold,
-                                                const Real* __restrict__ Snew, double* Sedge,
-                                                int src_mask) {
-  const int fi = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void frame2_node(const Geom& g, const Consts<Real>& c,
+                                            Real* __restrict__ B, const Real* __restrict__ Sold,
+                                            const Real* __restrict__ Snew, double* Sedge,
+                                            int src_mask, int fi) {
   if (fi >= g.frame_n) return;
   int x, y;
   frame_xy(g, fi, x, y);
@@ -596,6 +612,14 @@ __global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __
   }
 }
 
+template <class S, class Real>
+__global__ void __launch_bounds__(128) k_frame2(Geom g, Consts<Real> c, Real* __restrict__ B,
+                                                const Real* __restrict__ Sold,
+                                                const Real* __restrict__ Snew, double* Sedge,
+                                                int src_mask) {
+  frame2_node<S, Real>(g, c, B, Sold, Snew, Sedge, src_mask, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 __device__ inline void gamma_xy(const Geom& g, int t, int& x, int& y) {
   const int M = g.M, Gx = g.Lx + 2 * M;
   if (t < M * Gx) { y = t / Gx; x = t - y * Gx - M; y -= M; return; }
@@ -632,12 +656,12 @@ __device__ inline int q_slot(const Geom& g, int x, int y) {
 // Link mode with a PML (Sold != nullptr): the node also advances its accumulator
 // S^n = S^(n-1) + f_hat^n (slot frame_n + t) from the moments of its pre-collision state.
 template <class S, class Real, bool DEV, bool STREAM>
-__global__ void __launch_bounds__(128) k_gamma(Geom g, Consts<Real> c, BcParams bc,
-                                               const Real* __restrict__ A, Real* __restrict__ B,
-                                               const double* __restrict__ Vtgt,
-                                               const Real* __restrict__ Sold,
-                                               Real* __restrict__ Snew) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void gamma_node(const Geom& g, const Consts<Real>& c,
+                                           const BcParams& bc, const Real* __restrict__ A,
+                                           Real* __restrict__ B,
+                                           const double* __restrict__ Vtgt,
+                                           const Real* __restrict__ Sold,
+                                           Real* __restrict__ Snew, int t) {
   if (t >= g.ngamma) return;
   int x, y;
   gamma_xy(g, t, x, y);
@@ -702,19 +726,34 @@ __global__ void __launch_bounds__(128) k_gamma(Geom g, Consts<Real> c, BcParams 
   for (int i = 0; i < S::Q; ++i) B[(long long)i * g.plane + dst] = p[i];
 }
 
+template <class S, class Real, bool DEV, bool STREAM>
+__global__ void __launch_bounds__(128) k_gamma(Geom g, Consts<Real> c, BcParams bc,
+                                               const Real* __restrict__ A, Real* __restrict__ B,
+                                               const double* __restrict__ Vtgt,
+                                               const Real* __restrict__ Sold,
+                                               Real* __restrict__ Snew) {
+  gamma_node<S, Real, DEV, STREAM>(g, c, bc, A, B, Vtgt, Sold, Snew,
+                                   blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Periodic y axis: the M rows below y = 0 and above y = Ly - 1 (boundary columns included)
 // take the post-collision populations of the rows they image, PML term included, once every
 // other kernel of the step has written B. Thread = (direction, row pair j, column).
 template <class Real>
-__global__ void __launch_bounds__(256) k_wrap_y(Geom g, Real* __restrict__ B) {
+__device__ __forceinline__ void wrap_y_elem(const Geom& g, Real* __restrict__ B, long long t,
+                                            int dir) {
   const int Gx = g.Lx + 2 * g.M;
   const long long n = (long long)Gx * g.M;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int j = int(t / Gx) + 1, x = int(t % Gx) - g.M;
-  Real* plane = B + (long long)blockIdx.y * g.plane;
+  Real* plane = B + (long long)dir * g.plane;
   plane[gindex(g, x, -j)] = plane[gindex(g, x, g.Ly - j)];
   plane[gindex(g, x, g.Ly - 1 + j)] = plane[gindex(g, x, j - 1)];
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) k_wrap_y(Geom g, Real* __restrict__ B) {
+  wrap_y_elem<Real>(g, B, (long long)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------------------------------------------------------

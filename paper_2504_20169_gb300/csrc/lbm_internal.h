@@ -41,9 +41,45 @@ struct Dev {
   // optional timing: when ev is set, event 2k / 2k+1 are recorded around kernel class k
   // (0 characteristic targets, 1 interior, 2 frame phase 1, 3 frame phase 2, 4 boundary band)
   cudaEvent_t* ev;
+  // the context's one-member batch plan (its descriptors for buffer parity 0 and 1) and the
+  // parity of this launch; streaming steps run the boundary-side classes through it
+  const struct BatchPlan* plan;
+  int which;
 };
 
 constexpr int kKernelClasses = 5;
+
+// Characteristic-target work of one batch member (the batched RK4 launch).
+struct TgtDesc {
+  Geom g;
+  BcParams bc;
+  const double* Ue;
+  const double* Se;
+  double* V;
+};
+
+// Work list of a batch of instances with the same stencil, precision and PML gradient mode:
+// one launch per kernel class over a table of (member, tile / block) entries that spans all
+// instances (see lbm_batch_step). The member descriptors exist for the two buffer-parity
+// states the batch alternates between; everything lives in one device allocation.
+struct BatchPlan {
+  int n = 0;                  // members
+  void* desc[2] = {nullptr, nullptr};   // member descriptors, parity state 0 / 1
+  TgtDesc* tgt[2] = {nullptr, nullptr};
+  int* bulk_tab = nullptr;    // (member, bx, by)
+  int* frame_tab = nullptr;   // fused FP32 frame tiles: (member, tile)
+  int* f1_tab = nullptr;      // frame phase 1 blocks of 128 nodes: (member, block)
+  int* f2_tab = nullptr;      // frame phase 2 blocks (members with a PML): (member, block)
+  int* band_tab = nullptr;    // boundary-band blocks of 128 nodes: (member, block)
+  int* tgt_tab = nullptr;     // characteristic-target chunks: (member, chunk)
+  int* wrap_tab = nullptr;    // periodic-y row copies, blocks of 256: (member, block)
+  int n_bulk = 0, n_frame = 0, n_f1 = 0, n_f2 = 0, n_band = 0, n_tgt = 0, n_wrap = 0;
+  size_t frame_smem = 0, tgt_smem = 0;
+  int tgt_threads = 0, q = 0;
+  int tx = 32, by = 4;        // bulk tile shape (blockDim)
+  bool link = false;
+  void* mem = nullptr;
+};
 
 struct OpsTable {
   cudaError_t (*prepare)();   // kernel attributes on the current device
@@ -54,7 +90,25 @@ struct OpsTable {
   cudaError_t (*export_pop)(const Dev&, const void* src, double* out);
   cudaError_t (*import_pop)(const Dev&, const double* in, void* dst);
   int elem_size;
+  // batched execution (lbm_batch): build the plan of n members from their launch state in
+  // the two parity states (dev0[m], dev1[m]), launch one step of parity state `which`
+  // (boundary-side work forked onto aux / aux2 and joined back into st), free the plan
+  cudaError_t (*batch_plan)(const Dev* const* dev0, const Dev* const* dev1, int n, int tx,
+                            int by, BatchPlan* plan);
+  cudaError_t (*batch_step)(const BatchPlan& plan, int which, cudaStream_t st, cudaStream_t aux,
+                            cudaStream_t aux2, cudaEvent_t fork, cudaEvent_t join,
+                            cudaEvent_t join2);
 };
+
+void batch_plan_free(BatchPlan* plan);
+
+// Launch shape of the characteristic-target kernel of one grid: chunks (blocks), threads per
+// block, dynamic shared memory.
+void nrbc_shape(const Geom& g, int* chunks, int* threads, size_t* smem);
+
+// Batched characteristic targets: one block per table entry (member, chunk).
+cudaError_t launch_nrbc_batch(const TgtDesc* d, const int* tab, int n, bool fp32, int threads,
+                              size_t smem, cudaStream_t s);
 
 OpsTable ops_q37_f64();
 OpsTable ops_q37_f32();

@@ -66,12 +66,16 @@ __device__ inline void char_rate(const BcParams& bc, int variant, double out, co
 // bands wrap around (central tangential differences everywhere, halo taken modulo Ly).
 constexpr int kChunk = 32, kHalo = 4, kText = kChunk + 2 * kHalo;
 
+// (nrbc_chunk is the per-block work, shared with the batched launch over many instances;
+// chunk = index over the four bands' chunks, sm = 16 M kText doubles of shared memory.)
 template <class R>
-__global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
-                           const double* __restrict__ Se, double* __restrict__ Vg) {
+__device__ __forceinline__ void nrbc_chunk(const Geom& g, const BcParams& bc,
+                                           const double* __restrict__ Ue,
+                                           const double* __restrict__ Se,
+                                           double* __restrict__ Vg, int chunk, double* sm) {
   const int M = g.M, Lx = g.Lx, Ly = g.Ly;
   const int cw = (Ly + kChunk - 1) / kChunk, cs = (Lx + kChunk - 1) / kChunk;
-  int e, k = blockIdx.x;
+  int e, k = chunk;
   if (k < cw) e = 0;
   else if (k < 2 * cw) { e = 1; k -= cw; }
   else if (k < 2 * cw + cs) { e = 2; k -= 2 * cw; }
@@ -89,7 +93,6 @@ __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
   const int hi = wrap ? t0 + kChunk + kHalo : min(len, t0 + kChunk + kHalo);
   auto wr = [&](int tt) { return wrap ? ((tt % len) + len) % len : tt; };
   // shared state: [4 buffers][4 comps][M][kText] : V0, stage a, stage b, accumulator
-  extern __shared__ double sm[];
   const int plane = M * kText;
   auto at = [&](int buf, int q, int j, int t) -> double& {
     return sm[(buf * 4 + q) * plane + (j - 1) * kText + (t - lo)];
@@ -171,13 +174,42 @@ __global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
   }
 }
 
+template <class R>
+__global__ void k_nrbc_rk4(Geom g, BcParams bc, const double* __restrict__ Ue,
+                           const double* __restrict__ Se, double* __restrict__ Vg) {
+  extern __shared__ double sm[];
+  nrbc_chunk<R>(g, bc, Ue, Se, Vg, blockIdx.x, sm);
+}
+
+template <class R>
+__global__ void kb_nrbc_rk4(const TgtDesc* __restrict__ d, const int* __restrict__ tab) {
+  extern __shared__ double sm[];
+  const int m = tab[2 * blockIdx.x], chunk = tab[2 * blockIdx.x + 1];
+  const TgtDesc& t = d[m];
+  nrbc_chunk<R>(t.g, t.bc, t.Ue, t.Se, t.V, chunk, sm);
+}
+
+void nrbc_shape(const Geom& g, int* chunks, int* threads, size_t* smem) {
+  *chunks = 2 * ((g.Ly + kChunk - 1) / kChunk) + 2 * ((g.Lx + kChunk - 1) / kChunk);
+  *threads = (g.M * kText + 31) / 32 * 32;
+  *smem = sizeof(double) * 16 * g.M * kText;
+}
+
+cudaError_t launch_nrbc_batch(const TgtDesc* d, const int* tab, int n, bool fp32, int threads,
+                              size_t smem, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (fp32) kb_nrbc_rk4<float><<<n, threads, smem, s>>>(d, tab);
+  else kb_nrbc_rk4<double><<<n, threads, smem, s>>>(d, tab);
+  return cudaGetLastError();
+}
+
 // The four RK4 stages of one step in one launch; fp32 selects FP32 characteristic algebra
 // (targets and differences stay FP64).
 cudaError_t launch_nrbc_stages(const Dev& d, bool fp32, cudaStream_t s) {
   const Geom& g = d.g;
-  const int blocks = 2 * ((g.Ly + kChunk - 1) / kChunk) + 2 * ((g.Lx + kChunk - 1) / kChunk);
-  const int threads = (g.M * kText + 31) / 32 * 32;
-  const size_t smem = sizeof(double) * 16 * g.M * kText;
+  int blocks, threads;
+  size_t smem;
+  nrbc_shape(g, &blocks, &threads, &smem);
   if (fp32)
     k_nrbc_rk4<float><<<blocks, threads, smem, s>>>(g, d.bc, d.Uedge_in, d.Sedge_in, d.Vtgt);
   else

@@ -1,8 +1,11 @@
 // Launchers of one (stencil, precision) combination. Instantiated once per combination in the
 // ops_*.cu translation units so they compile in parallel.
 #pragma once
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
@@ -195,6 +198,93 @@ __global__ void k_import(Geom g, Consts<Real> c, const double* __restrict__ in, 
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Batched execution: one launch per kernel class over a table spanning every instance of the
+// batch. Each block reads its (member, tile) entry and runs the same per-node / per-tile body
+// as the single-instance kernels, so every member computes bit for bit what it computes alone.
+// ------------------------------------------------------------------------------------------
+template <class Real>
+struct MemberDev {
+  Geom g;
+  Consts<Real> c;
+  BcParams bc;
+  FrameTiles ft;
+  const Real* A;
+  Real* B;
+  const Real* Sold;
+  Real* Snew;
+  double* Vtgt;
+  double* Uedge_out;
+  double* Sedge_out;
+  int* flag;
+  int src_mask;
+};
+
+template <class S, class Real, bool DEV>
+__global__ void __launch_bounds__(256) kb_bulk(const MemberDev<Real>* __restrict__ mem,
+                                               const int* __restrict__ tab) {
+  const int* e = tab + 3 * blockIdx.x;
+  const MemberDev<Real>& md = mem[e[0]];
+  const Geom g = md.g;
+  const int x0 = (g.Fw / 32) * 32;
+  bulk_node<S, Real, DEV, true>(g, md.c, md.A, md.B, md.flag,
+                                x0 + e[1] * blockDim.x + threadIdx.x,
+                                g.Fs + e[2] * blockDim.y + threadIdx.y);
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) kb_pml_fused(const MemberDev<float>* __restrict__ mem,
+                                                    const int* __restrict__ tab) {
+  extern __shared__ float smem[];
+  const int* e = tab + 2 * blockIdx.x;
+  const MemberDev<float>& md = mem[e[0]];
+  const Geom g = md.g;
+  pml_fused_tile<S, true>(g, md.c, md.ft, md.A, md.B, md.Sold, md.Snew, md.Uedge_out,
+                          md.bc.bc == 2 ? 1 : 0, md.flag, md.Sedge_out, md.src_mask, e[1], smem);
+}
+
+template <class S, class Real, bool DEV>
+__global__ void __launch_bounds__(128) kb_frame1(const MemberDev<Real>* __restrict__ mem,
+                                                 const int* __restrict__ tab) {
+  const int* e = tab + 2 * blockIdx.x;
+  const MemberDev<Real>& md = mem[e[0]];
+  const Geom g = md.g;
+  frame1_node<S, Real, DEV, true>(g, md.c, md.A, md.B, md.Sold, md.Snew, md.Uedge_out,
+                                  md.bc.bc == 2 ? 1 : 0, md.flag, md.Sedge_out, md.src_mask,
+                                  e[1] * blockDim.x + threadIdx.x);
+}
+
+template <class S, class Real>
+__global__ void __launch_bounds__(128) kb_frame2(const MemberDev<Real>* __restrict__ mem,
+                                                 const int* __restrict__ tab) {
+  const int* e = tab + 2 * blockIdx.x;
+  const MemberDev<Real>& md = mem[e[0]];
+  const Geom g = md.g;
+  frame2_node<S, Real>(g, md.c, md.B, md.Sold, md.Snew, md.Sedge_out, md.src_mask,
+                       e[1] * blockDim.x + threadIdx.x);
+}
+
+template <class S, class Real, bool DEV>
+__global__ void __launch_bounds__(128) kb_gamma(const MemberDev<Real>* __restrict__ mem,
+                                                const int* __restrict__ tab) {
+  const int* e = tab + 2 * blockIdx.x;
+  const MemberDev<Real>& md = mem[e[0]];
+  const Geom g = md.g;
+  const bool link = g.link && has_pml(g);
+  gamma_node<S, Real, DEV, true>(g, md.c, md.bc, md.A, md.B, md.Vtgt,
+                                 link ? md.Sold : nullptr, link ? md.Snew : nullptr,
+                                 e[1] * blockDim.x + threadIdx.x);
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) kb_wrap_y(const MemberDev<Real>* __restrict__ mem,
+                                                 const int* __restrict__ tab) {
+  const int* e = tab + 2 * blockIdx.x;
+  const MemberDev<Real>& md = mem[e[0]];
+  const Geom g = md.g;
+  wrap_y_elem<Real>(g, md.B, (long long)e[1] * blockDim.x + threadIdx.x, blockIdx.y);
+}
+
 template <class S, class Real, bool DEV>
 struct Ops {
   static const Consts<Real>& consts(const Dev& d) {
@@ -225,12 +315,41 @@ struct Ops {
     // Appendix PML source terms: only with a characteristic BC and a PML
     const int src_mask = (d.bc.bc == 2 && has_pml(g)) ? (d.bc.pml_source & 7) : 0;
     mark(0, bs);
-    if (STREAM && d.bc.bc == 2) launch_nrbc_stages(d, sizeof(Real) == 4, bs);
+    // Streaming steps of a context run the boundary-side classes through the table-driven
+    // kernels of its one-member plan (the kernels a batch runs), so that a context computes
+    // bit for bit the same alone and in any batch; the interior kernel is the same either way.
+    const BatchPlan* pl = STREAM ? d.plan : nullptr;
+    const MemberDev<Real>* pm = pl ? static_cast<const MemberDev<Real>*>(pl->desc[d.which]) : nullptr;
+    if (pl) {
+      launch_nrbc_batch(pl->tgt[d.which], pl->tgt_tab, pl->n_tgt, sizeof(Real) == 4,
+                        pl->tgt_threads, pl->tgt_smem, bs);
+    } else if (STREAM && d.bc.bc == 2) {
+      launch_nrbc_stages(d, sizeof(Real) == 4, bs);
+    }
     mark(1, bs);
     mark(4, fs);
+    if (pl) {
+      if constexpr (DEV) {
+        if (pl->n_frame)
+          kb_pml_fused<S><<<pl->n_frame, 256, pl->frame_smem, fs>>>(
+              reinterpret_cast<const MemberDev<float>*>(pm), pl->frame_tab);
+      }
+      if (pl->n_f1) kb_frame1<S, Real, DEV><<<pl->n_f1, 128, 0, fs>>>(pm, pl->f1_tab);
+      mark(5, fs);
+      auto band_b = [&]() {
+        mark(8, bs);
+        if (pl->n_band) kb_gamma<S, Real, DEV><<<pl->n_band, 128, 0, bs>>>(pm, pl->band_tab);
+        mark(9, bs);
+      };
+      if (link) band_b();
+      mark(6, fs);
+      if (pl->n_f2) kb_frame2<S, Real><<<pl->n_f2, 128, 0, fs>>>(pm, pl->f2_tab);
+      mark(7, fs);
+      if (!link) band_b();
+    }
     bool fused = false;
     if constexpr (DEV) {
-      if (has_pml(g) && !link) {
+      if (!pl && has_pml(g) && !link) {
         // FP32: single-pass frame (tile + halo in shared memory)
         const FrameTiles ft = make_frame_tiles(g, 256);
         const size_t smem = pml_fused_smem<S>(ft);
@@ -240,11 +359,11 @@ struct Ops {
         fused = true;
       }
     }
-    if (!fused)
+    if (!fused && !pl)
       k_frame1<S, Real, DEV, STREAM><<<(g.frame_n + 127) / 128, 128, 0, fs>>>(
           g, c, A, B, static_cast<const Real*>(d.Sold), static_cast<Real*>(d.Snew), d.Uedge_out,
           d.bc.bc == 2 ? 1 : 0, d.flag, d.Sedge_out, src_mask);
-    mark(5, fs);
+    if (!pl) mark(5, fs);
     auto band = [&]() {
       mark(8, bs);
       k_gamma<S, Real, DEV, STREAM><<<(g.ngamma + 127) / 128, 128, 0, bs>>>(
@@ -252,14 +371,16 @@ struct Ops {
           link ? static_cast<Real*>(d.Snew) : nullptr);
       mark(9, bs);
     };
-    if (link) band();
-    mark(6, fs);
-    if (has_pml(g) && !fused)
-      k_frame2<S, Real><<<(g.frame_n + 127) / 128, 128, 0, fs>>>(
-          g, c, B, static_cast<const Real*>(d.Sold), static_cast<const Real*>(d.Snew),
-          d.Sedge_out, src_mask);
-    mark(7, fs);
-    if (!link) band();
+    if (!pl) {
+      if (link) band();
+      mark(6, fs);
+      if (has_pml(g) && !fused)
+        k_frame2<S, Real><<<(g.frame_n + 127) / 128, 128, 0, fs>>>(
+            g, c, B, static_cast<const Real*>(d.Sold), static_cast<const Real*>(d.Snew),
+            d.Sedge_out, src_mask);
+      mark(7, fs);
+      if (!link) band();
+    }
     const int nbx = (g.Lx - g.Fe - (g.Fw / 32) * 32 + 31) / 32;
     const int ny_in = g.Ly - g.Fs - g.Fn;
     constexpr int BY = 4;
@@ -277,7 +398,9 @@ struct Ops {
         cudaStreamWaitEvent(d.st, d.join2, 0);
       }
     }
-    if (g.py) {
+    if (pl) {
+      if (pl->n_wrap) kb_wrap_y<Real><<<dim3(pl->n_wrap, S::Q), 256, 0, d.st>>>(pm, pl->wrap_tab);
+    } else if (g.py) {
       const long long n = (long long)(g.Lx + 2 * g.M) * g.M;
       k_wrap_y<Real><<<dim3(unsigned((n + 255) / 256), S::Q), 256, 0, d.st>>>(g, B);
     }
@@ -335,9 +458,165 @@ struct Ops {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_pml_fused<S, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_pml_fused<S>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       return e;
     }
     return cudaSuccess;
+  }
+
+  // ---------------------------------------------------------------- batched execution
+  static MemberDev<Real> member_of(const Dev& d) {
+    MemberDev<Real> m;
+    std::memset(&m, 0, sizeof m);
+    m.g = d.g;
+    m.c = consts(d);
+    m.bc = d.bc;
+    m.ft = make_frame_tiles(d.g, 256);
+    m.A = static_cast<const Real*>(d.A);
+    m.B = static_cast<Real*>(d.B);
+    m.Sold = static_cast<const Real*>(d.Sold);
+    m.Snew = static_cast<Real*>(d.Snew);
+    m.Vtgt = d.Vtgt;
+    m.Uedge_out = d.Uedge_out;
+    m.Sedge_out = d.Sedge_out;
+    m.flag = d.flag;
+    m.src_mask = (d.bc.bc == 2 && has_pml(d.g)) ? (d.bc.pml_source & 7) : 0;
+    return m;
+  }
+
+  static bool fused_of(const Geom& g) { return DEV && has_pml(g) && !g.link; }
+
+  static cudaError_t batch_plan(const Dev* const* dev0, const Dev* const* dev1, int n, int tx,
+                                int by, BatchPlan* plan) {
+    BatchPlan p;
+    p.n = n;
+    p.tx = tx;
+    p.by = by;
+    p.q = S::Q;
+    p.link = n > 0 && dev0[0]->g.link;
+    std::vector<int> bulk, frame, f1, f2, band, tgt, wrap;
+    for (int m = 0; m < n; ++m) {
+      const Geom& g = dev0[m]->g;
+      const int x0 = (g.Fw / 32) * 32;
+      const int nbx = (g.Lx - g.Fe - x0 + tx - 1) / tx, nby = (g.Ly - g.Fs - g.Fn + by - 1) / by;
+      if (g.Lx - g.Fe - x0 > 0 && g.Ly - g.Fs - g.Fn > 0)
+        for (int j = 0; j < nby; ++j)
+          for (int i = 0; i < nbx; ++i) bulk.insert(bulk.end(), {m, i, j});
+      if (fused_of(g)) {
+        const FrameTiles ft = make_frame_tiles(g, 256);
+        const int nt = frame_tile_count(ft);
+        for (int k = 0; k < nt; ++k) frame.insert(frame.end(), {m, k});
+        p.frame_smem = std::max(p.frame_smem, pml_fused_smem<S>(ft));
+      } else {
+        for (int b = 0; b < (g.frame_n + 127) / 128; ++b) f1.insert(f1.end(), {m, b});
+        if (has_pml(g))
+          for (int b = 0; b < (g.frame_n + 127) / 128; ++b) f2.insert(f2.end(), {m, b});
+      }
+      for (int b = 0; b < (g.ngamma + 127) / 128; ++b) band.insert(band.end(), {m, b});
+      if (dev0[m]->bc.bc == 2) {
+        int chunks, threads;
+        size_t smem;
+        nrbc_shape(g, &chunks, &threads, &smem);
+        for (int k = 0; k < chunks; ++k) tgt.insert(tgt.end(), {m, k});
+        p.tgt_threads = std::max(p.tgt_threads, threads);
+        p.tgt_smem = std::max(p.tgt_smem, smem);
+      }
+      if (g.py) {
+        const long long nw = (long long)(g.Lx + 2 * g.M) * g.M;
+        for (int b = 0; b < (int)((nw + 255) / 256); ++b) wrap.insert(wrap.end(), {m, b});
+      }
+    }
+    p.n_bulk = (int)bulk.size() / 3;
+    p.n_frame = (int)frame.size() / 2;
+    p.n_f1 = (int)f1.size() / 2;
+    p.n_f2 = (int)f2.size() / 2;
+    p.n_band = (int)band.size() / 2;
+    p.n_tgt = (int)tgt.size() / 2;
+    p.n_wrap = (int)wrap.size() / 2;
+    // one device allocation: descriptors (2 parity states), target descriptors, tables
+    std::vector<MemberDev<Real>> d0(n), d1(n);
+    std::vector<TgtDesc> t0(n), t1(n);
+    for (int m = 0; m < n; ++m) {
+      d0[m] = member_of(*dev0[m]);
+      d1[m] = member_of(*dev1[m]);
+      t0[m] = TgtDesc{dev0[m]->g, dev0[m]->bc, dev0[m]->Uedge_in, dev0[m]->Sedge_in, dev0[m]->Vtgt};
+      t1[m] = TgtDesc{dev1[m]->g, dev1[m]->bc, dev1[m]->Uedge_in, dev1[m]->Sedge_in, dev1[m]->Vtgt};
+    }
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t bd = al(sizeof(MemberDev<Real>) * n), bt = al(sizeof(TgtDesc) * n);
+    const std::vector<int>* tabs[7] = {&bulk, &frame, &f1, &f2, &band, &tgt, &wrap};
+    size_t total = 2 * bd + 2 * bt;
+    for (auto* t : tabs) total += al(sizeof(int) * t->size() + 4);
+    char* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, total);
+    if (e != cudaSuccess) return e;
+    p.mem = mem;
+    size_t off = 0;
+    auto put = [&](const void* src, size_t bytes, size_t slot) {
+      void* dst = mem + off;
+      if (bytes && e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+      off += slot;
+      return dst;
+    };
+    p.desc[0] = put(d0.data(), sizeof(MemberDev<Real>) * n, bd);
+    p.desc[1] = put(d1.data(), sizeof(MemberDev<Real>) * n, bd);
+    p.tgt[0] = static_cast<TgtDesc*>(put(t0.data(), sizeof(TgtDesc) * n, bt));
+    p.tgt[1] = static_cast<TgtDesc*>(put(t1.data(), sizeof(TgtDesc) * n, bt));
+    int** dst[7] = {&p.bulk_tab, &p.frame_tab, &p.f1_tab, &p.f2_tab, &p.band_tab, &p.tgt_tab,
+                    &p.wrap_tab};
+    for (int k = 0; k < 7; ++k)
+      *dst[k] = static_cast<int*>(put(tabs[k]->data(), sizeof(int) * tabs[k]->size(),
+                                      al(sizeof(int) * tabs[k]->size() + 4)));
+    if (e != cudaSuccess) {
+      cudaFree(mem);
+      return e;
+    }
+    *plan = p;
+    return cudaSuccess;
+  }
+
+  static cudaError_t batch_step(const BatchPlan& p, int which, cudaStream_t st, cudaStream_t aux,
+                                cudaStream_t aux2, cudaEvent_t fork, cudaEvent_t join,
+                                cudaEvent_t join2) {
+    const MemberDev<Real>* mem = static_cast<const MemberDev<Real>*>(p.desc[which]);
+    const cudaStream_t bs = aux ? aux : st;
+    const cudaStream_t fs = p.link ? bs : (aux2 ? aux2 : bs);
+    if (aux) {
+      cudaEventRecord(fork, st);
+      cudaStreamWaitEvent(aux, fork, 0);
+      if (aux2) cudaStreamWaitEvent(aux2, fork, 0);
+    }
+    // characteristic targets, then (printed gradient) the boundary band, on bs
+    cudaError_t e = launch_nrbc_batch(p.tgt[which], p.tgt_tab, p.n_tgt, sizeof(Real) == 4,
+                                      p.tgt_threads, p.tgt_smem, bs);
+    if (e != cudaSuccess) return e;
+    auto band = [&]() {
+      if (p.n_band) kb_gamma<S, Real, DEV><<<p.n_band, 128, 0, bs>>>(mem, p.band_tab);
+    };
+    if (!p.link) band();
+    // the frame on fs
+    if constexpr (DEV) {
+      if (p.n_frame)
+        kb_pml_fused<S><<<p.n_frame, 256, p.frame_smem, fs>>>(mem, p.frame_tab);
+    }
+    if (p.n_f1) kb_frame1<S, Real, DEV><<<p.n_f1, 128, 0, fs>>>(mem, p.f1_tab);
+    if (p.link) band();
+    if (p.n_f2) kb_frame2<S, Real><<<p.n_f2, 128, 0, fs>>>(mem, p.f2_tab);
+    // the interiors of every member on st
+    if (p.n_bulk)
+      kb_bulk<S, Real, DEV><<<p.n_bulk, dim3(p.tx, p.by), 0, st>>>(mem, p.bulk_tab);
+    if (aux) {
+      cudaEventRecord(join, aux);
+      cudaStreamWaitEvent(st, join, 0);
+      if (aux2) {
+        cudaEventRecord(join2, aux2);
+        cudaStreamWaitEvent(st, join2, 0);
+      }
+    }
+    if (p.n_wrap) kb_wrap_y<Real><<<dim3(p.n_wrap, S::Q), 256, 0, st>>>(mem, p.wrap_tab);
+    return cudaGetLastError();
   }
 
   static OpsTable table() {
@@ -349,6 +628,8 @@ struct Ops {
     t.export_pop = &export_pop;
     t.import_pop = &import_pop;
     t.elem_size = sizeof(Real);
+    t.batch_plan = &batch_plan;
+    t.batch_step = &batch_step;
     return t;
   }
 };

@@ -75,19 +75,21 @@ inline size_t pml_fused_smem(const FrameTiles& ft) {
   return sizeof(float) * ((size_t)S::Q * ft.ext_max + 7 * 256);
 }
 
+// One frame tile (tile = index over the four bands' tiles) on one block; smem holds
+// pml_fused_smem bytes. Shared with the batched launch over many instances.
 template <class S, bool STREAM>
-__global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, FrameTiles ft,
-                                                   const float* __restrict__ A,
-                                                   float* __restrict__ B,
-                                                   const float* __restrict__ Sold,
-                                                   float* __restrict__ Snew, double* Uedge,
-                                                   int save_edges, int* flag, double* Sedge,
-                                                   int src_mask) {
-  extern __shared__ float smem[];
+__device__ __forceinline__ void pml_fused_tile(const Geom& g, const Consts<float>& c,
+                                               const FrameTiles& ft,
+                                               const float* __restrict__ A,
+                                               float* __restrict__ B,
+                                               const float* __restrict__ Sold,
+                                               float* __restrict__ Snew, double* Uedge,
+                                               int save_edges, int* flag, double* Sedge,
+                                               int src_mask, int tile, float* smem) {
   // ---- tile of this block
   int x0, y0, tw, th, band;  // band 0 bottom, 1 top, 2 left, 3 right
   {
-    int k = blockIdx.x;
+    int k = tile;
     band = 0;
     while (band < 3 && k >= ft.b[band].n) k -= ft.b[band++].n;
     const BandTiles& bt = ft.b[band];
@@ -224,6 +226,19 @@ __global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, Fram
     smom[3] *= 0.5 * double(c.r2);
     put_pml_source(g, Sedge, x, y, smom, false);
   }
+}
+
+template <class S, bool STREAM>
+__global__ void __launch_bounds__(256) k_pml_fused(Geom g, Consts<float> c, FrameTiles ft,
+                                                   const float* __restrict__ A,
+                                                   float* __restrict__ B,
+                                                   const float* __restrict__ Sold,
+                                                   float* __restrict__ Snew, double* Uedge,
+                                                   int save_edges, int* flag, double* Sedge,
+                                                   int src_mask) {
+  extern __shared__ float smem[];
+  pml_fused_tile<S, STREAM>(g, c, ft, A, B, Sold, Snew, Uedge, save_edges, flag, Sedge, src_mask,
+                            blockIdx.x, smem);
 }
 
 }  // namespace lbm

@@ -21,12 +21,11 @@ from .solver import _BC, _PREC, Solver, _check
 
 
 def estimate_bytes(case, precision="fp32dev", q=37):
-    """Device bytes lbm_create would allocate for a workloads.Case (no allocation)."""
-    n = C.c_size_t()
-    grid = L.lbm_grid(case.nx, case.ny)
-    _check(L.lib().lbm_estimate_bytes(C.byref(grid), q, case.W, _BC[case.bc], _PREC[precision],
-                                      C.byref(n)))
-    return int(n.value)
+    """Device bytes lbm_create would allocate for a workloads.Case (lbm_estimate_bytes_bc: no
+    allocation; counts the link gradient's wider accumulator)."""
+    from .solver import estimate_bytes as est
+    return int(est(case.nx, case.ny, case.W, q=q, bc=case.bc, precision=precision,
+                   pml_grad=getattr(case, "pml_grad", "central")))
 
 
 class Batch:
@@ -42,6 +41,17 @@ class Batch:
     def set(self, solvers):
         arr = (C.c_void_p * max(1, len(solvers)))(*[s.ctx.value for s in solvers])
         _check(L.lib().lbm_batch_set(self.h, arr, len(solvers)))
+
+    def tile(self, tx=0, by=0):
+        """Interior block shape of the batched launch (0, 0: tuned or default)."""
+        _check(L.lib().lbm_batch_tile(self.h, int(tx), int(by)))
+
+    def autotune(self, steps=5):
+        """Time the candidate interior block shapes on this batch (advances every member by
+        8 (steps + 1) steps) and keep the fastest; returns (tx, by)."""
+        tx, by = C.c_int(), C.c_int()
+        _check(L.lib().lbm_batch_autotune(self.h, int(steps), C.byref(tx), C.byref(by)))
+        return tx.value, by.value
 
     def step(self, n):
         """Returns True, or False if a member flagged an unphysical state (nobody stepped)."""

@@ -95,3 +95,40 @@ def test_stress_8192_fp32_runs_and_matches_sampled_oracle_windows():
         worst = max(worst, abs(got[0][y, x] - ref[0]), abs(got[1][y, x] - ref[1]),
                     abs(got[2][y, x] - ref[2]), abs(got[3][y, x] - ref[3]))
     assert worst < 1e-5
+
+
+def test_full_grid_elementwise_vs_oracle_at_benchmark_size():
+    """Every node of F after 10 steps of the benchmark configuration (2048^2 bulk + PML 32,
+    cubic sigma 0.1, east CBC relax, tau 0.55, Mach 0.3 vortex): interior, frame and boundary
+    kernels and the characteristic targets at their full-size tile and chunk shapes, FP64 and
+    FP32, against one oracle run (about 10 s of CPU per oracle step)."""
+    import os
+    from parity_helpers import PERT_TOL, TOL, field_errors
+    try:
+        ram = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError):
+        ram = 0
+    if ram and ram < 48e9:
+        pytest.skip("the oracle at 2112^2 needs about 20 GB of host memory")
+    c = wl.vortex_2048()
+    fields = c.fields()
+    kw = case_kwargs(nx=c.nx, ny=c.ny, W=c.W, tau=c.tau, sigma_max=c.sigma_max,
+                     sigma_power=c.sigma_power, bc=c.bc, nrbc_edges=c.nrbc_edges, beta=c.beta,
+                     mean=c.mean)
+    steps = 10
+    o = OracleLBM(c.nx, c.ny, c.W, c.tau, c.sigma_max, c.sigma_power, c.bc,
+                  nrbc_edges=c.nrbc_edges, beta=c.beta, mean=c.mean)
+    o.init(*fields)
+    o.step(steps)
+    ora = o.fields()
+    del o
+    for precision in ("fp64", "fp32dev"):
+        with make_solver(kw, precision) as s:
+            s.init(*fields)
+            s.step(steps)
+            gpu = s.moments()
+        full, pert = field_errors(gpu, ora)
+        print(f"full grid {precision} full={['%.2e' % e for e in full]} "
+              f"pert={['%.2e' % e for e in pert]}")
+        assert max(full) < TOL[precision], full
+        assert max(pert) < PERT_TOL[precision], pert

@@ -116,3 +116,78 @@ def test_engine_serves_a_poisson_stream():
     s = summarize(reqs, eng.wall, eng.sites_steps)
     assert s["done"] + s["unstable"] == 12 and s["rejected"] == 0
     assert s["latency_p99_s"] >= s["latency_p50_s"] > 0
+
+
+MIX = [  # one group per (stencil, precision, gradient mode) with ragged members
+    (case_kwargs(nx=64, ny=48, W=6, tau=0.7, sigma_max=0.1, bc="zg"), "fp32dev"),
+    (case_kwargs(nx=96, ny=80, W=12, tau=0.8, sigma_max=0.05, bc="nrbc", nrbc_edges=(0, 1, 0, 0),
+                 beta=0.3, mean=(1.0, 0.2, 0.0, 1.0)), "fp32dev"),
+    (case_kwargs(nx=50, ny=70, W=5, tau=0.75, sigma_max=0.2, sigma_power=2, bc="zg",
+                 pml_grad="link"), "fp32dev"),
+    (case_kwargs(nx=40, ny=40, W=0, tau=0.6, sigma_max=0.0, bc="nrbc", nrbc_edges=(1, 0, 0, 1),
+                 beta=0.2, mean=(1.0, 0.1, 0.0, 1.0)), "fp32dev"),
+    (case_kwargs(nx=60, ny=12, W=8, tau=0.8, sigma_max=0.05, sigma_power=2, bc="nrbc",
+                 mean=(1.0, 0.05, 0.0, 1.0), periodic_y=True, pml_grad="link"), "fp64"),
+    (case_kwargs(nx=36, ny=44, W=4, tau=0.7, sigma_max=0.1, bc="zg", q=17), "fp32dev"),
+]
+
+
+def _mix_fields(kw):
+    if kw["periodic_y"]:
+        return wl.density_step(kw["nx"], kw["ny"], Ma=0.05, W=kw["W"], Wy=0)
+    return wl.random_smooth_state(kw["nx"], kw["ny"], kw["W"], seed=kw["nx"], du=0.03,
+                                  mean_u=(kw["mean"][1], 0.0))
+
+
+def _alone(kw, prec, steps):
+    with make_solver(kw, prec) as s:
+        s.init(*_mix_fields(kw))
+        s.step(steps)
+        return s.moments()
+
+
+@pytest.mark.parametrize("tile", [(32, 4), (128, 1), (64, 2), (32, 8)])
+def test_batched_groups_equal_alone_for_every_tile_shape(tile):
+    """Mixed stencils, precisions and gradient modes in one batch (four groups); the interior
+    block shape never changes a bit; a member stepped on its own between batch steps makes the
+    batch rebuild its plans."""
+    from paper_2504_20169_gb300.serving import Batch
+    solvers = [make_solver(kw, prec) for kw, prec in MIX]
+    for (kw, prec), s in zip(MIX, solvers):
+        s.init(*_mix_fields(kw))
+    b = Batch()
+    b.tile(*tile)
+    b.set(solvers)
+    assert b.step(13)
+    solvers[2].step(3)                  # out-of-band step of one member
+    assert b.step(10)
+    got = [s.moments() for s in solvers]
+    b.close()
+    for s in solvers:
+        s.close()
+    for k, (kw, prec) in enumerate(MIX):
+        ref = _alone(kw, prec, 26 if k == 2 else 23)
+        for g, r in zip(got[k], ref):
+            assert np.array_equal(g, r), (k, tile)
+
+
+def test_autotune_picks_a_shape_and_changes_nothing():
+    from paper_2504_20169_gb300.serving import Batch
+    solvers = [make_solver(kw, prec) for kw, prec in MIX[:3]]
+    for (kw, prec), s in zip(MIX[:3], solvers):
+        s.init(*_mix_fields(kw))
+    b = Batch()
+    b.set(solvers)
+    tx, by = b.autotune(steps=2)
+    assert tx in (32, 64, 128, 256) and by >= 1 and tx * by <= 256
+    assert b.step(5)
+    got = [s.moments() for s in solvers]
+    steps = [s.steps for s in solvers]
+    b.close()
+    for s in solvers:
+        s.close()
+    assert steps == [8 * 3 + 5] * 3
+    for k, (kw, prec) in enumerate(MIX[:3]):
+        ref = _alone(kw, prec, steps[k])
+        for g, r in zip(got[k], ref):
+            assert np.array_equal(g, r), k

@@ -44,6 +44,43 @@ def test_noalloc_totals_match_lbm_reduce_on_two_calls():
             assert got[4] == ref[4] and got[5] == ref[5] and got[6] == ref[6]
 
 
+def test_noalloc_large_field_with_bad_entries_matches_numpy():
+    """n = 2^21 + 5 values (more than 1024 blocks x 256 threads, so the grid-stride loop goes
+    round more than once and the second pass folds all 1024 partial rows), with non-positive
+    and non-finite entries: sums against numpy in FP64 (rtol 1e-12; NaN where numpy gives NaN),
+    minima (fmin ignores NaN, like numpy.nanmin) and the bad-entry count exactly; two calls."""
+    import torch
+    from paper_2504_20169_gb300 import _lib as L
+    n = (1 << 21) + 5
+    rng = np.random.default_rng(3)
+    rho = rng.uniform(0.5, 1.5, n)
+    ux = rng.uniform(-0.3, 0.3, n)
+    uy = rng.uniform(-0.3, 0.3, n)
+    T = rng.uniform(0.8, 1.2, n)
+    bad = rng.choice(n, size=9, replace=False)
+    rho[bad[:3]] = [-0.5, 0.0, -2.0]
+    T[bad[3:6]] = [0.0, -1.0, 2e30]
+    for field in (True, False):
+        if field:
+            T2 = T.copy()
+            T2[bad[6]] = np.nan
+        else:
+            T2 = T
+        want_sum = [rho.sum(), (rho * ux).sum(), (rho * uy).sum(),
+                    (0.5 * rho * (ux * ux + uy * uy + 2.0 * T2)).sum()]
+        want_min = [np.nanmin(rho), np.nanmin(T2)]
+        ok = (rho > 0) & (T2 > 0) & (rho < 1e30) & (T2 < 1e30)
+        want_bad = float(np.count_nonzero(~ok))
+        dev = [torch.from_numpy(a).cuda() for a in (rho, ux, uy, T2)]
+        for call in range(2):
+            out = torch.full((7,), 123.0, dtype=torch.float64, device="cuda")
+            assert _call(L, dev, out) == L.LBM_OK, L.lib().lbm_last_error(None)
+            got = out.cpu().numpy()
+            assert np.allclose(got[:4], want_sum, rtol=1e-12, atol=0, equal_nan=True), (got, want_sum)
+            assert got[4] == want_min[0] and got[5] == want_min[1]
+            assert got[6] == want_bad
+
+
 def test_noalloc_rejects_sizes_beyond_its_maximum():
     import torch
     from paper_2504_20169_gb300 import _lib as L
