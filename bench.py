@@ -419,31 +419,78 @@ def fp64_flops_per_node():
     return 125 + 27 + 476
 
 
+def _served_error(reqs, ids, precision_ref="fp64"):
+    """Field error of served FP32 results against the same requests run alone in FP64 (bulk:
+    relative L2 of rho and T, velocity L2 over max(||u_ref||, c_s sqrt(N) / 10)); max over the
+    sampled requests that finished."""
+    import numpy as np
+    from paper_2504_20169_gb300 import Solver
+    worst = {"rho": 0.0, "ux": 0.0, "uy": 0.0, "T": 0.0}
+    n = 0
+    for r in reqs:
+        if r.rid not in ids or r.status != "done" or r.result is None:
+            continue
+        c = r.case
+        with Solver(c.nx, c.ny, c.W, c.tau, c.sigma_max, c.sigma_power, c.bc, 37, c.nrbc_edges,
+                    c.beta, c.mean, precision=precision_ref,
+                    pml_grad=getattr(c, "pml_grad", "central")) as s:
+            s.init(*c.fields())
+            s.step(r.steps)
+            ref = s.moments(region="bulk")
+        n += 1
+        for k, name in enumerate(("rho", "ux", "uy", "T")):
+            a, b = r.result[k], ref[k]
+            den = np.sqrt(np.sum(b * b))
+            if name in ("ux", "uy"):
+                den = max(den, 0.1 * np.sqrt(b.size))
+            worst[name] = max(worst[name], float(np.sqrt(np.sum((a - b) ** 2)) / den))
+    return {"samples": n, "max_rel_l2_vs_fp64": {k: float(f"{v:.3e}") for k, v in worst.items()}}
+
+
 def serving_runs(args):
-    """Batched sweep (32 seeded uneven instances, all admitted at t = 0, 150 steps each) and a
-    seeded Poisson request stream (48 requests at 50/s, bulk 64..1024, 100..300 steps), both in
-    FP32 deviation storage through the continuous-batching loop."""
+    """The batched sweep at its stated size (256 seeded uneven instances, admitted at t = 0,
+    1000 steps) and the Poisson request stream at its stated size (500 requests at 50/s, bulk
+    64..2048, PML 8..64) with the request lengths scaled from 1k..20k to 100..2000 steps, then
+    the same stream at a sustainable 5/s (150 requests). Both use the link-integrated PML
+    gradient and PNR-LODI on every characteristic edge: the printed gradient and CBC relax do
+    not survive such lengths (long-run entry). FP32 deviation storage through the
+    continuous-batching loop. Each section samples its smallest finished requests and reruns
+    them alone in FP64."""
     import workloads as wl
     from paper_2504_20169_gb300.serving import Engine, Request, summarize
-    sweep = wl.batched_sweep(count=32, seed=0, steps=150)
+    sweep = wl.batched_sweep(count=256, seed=0, steps=1000, pml_grad="link",
+                             nrbc_edges=(0, 0, 0, 0))
     reqs = [Request(k, 0.0, c, c.steps) for k, c in enumerate(sweep)]
-    eng = Engine(budget_bytes=100e9, precision="fp32dev", chunk=150, keep_fields=False)
+    sample = {r.rid for r in sorted(reqs, key=lambda r: r.case.nx)[:4]}
+    eng = Engine(budget_bytes=200e9, precision="fp32dev", chunk=250, keep_ids=sample,
+                 lookahead=len(reqs))
     eng.run(reqs)
     eng.close()
     b = summarize(reqs, eng.wall, eng.sites_steps, eng.step_seconds)
-    b["what"] = "32 instances of the seeded batched sweep (N 128..1024, W 4..64, ZG/NRBC, " \
-                "pulse/vortex), 150 steps each, one combined graph per step; wall clock " \
-                "includes admission (host IC + upload) and retirement"
-    stream = wl.request_stream(48, rate=50.0, seed=0, nmax=1024, smin=100, smax=300)
-    reqs = [Request(k, t, c, c.steps) for k, (t, c) in enumerate(stream)]
-    eng = Engine(budget_bytes=40e9, precision="fp32dev", chunk=50, keep_fields=False)
-    eng.run(reqs)
-    eng.close()
-    sv = summarize(reqs, eng.wall, eng.sites_steps, eng.step_seconds)
-    sv["what"] = "Poisson stream 50/s, 48 requests, bulk log-uniform 64..1024, PML 8..64, " \
-                 "100..300 steps, 40 GB admission budget, chunks of 50 steps; latency from " \
-                 "arrival to fields on the host"
-    return b, sv
+    b["error"] = _served_error(reqs, sample)
+    b["what"] = "256 instances of the seeded batched sweep (N 128..1024, W 4..64, sigma_max " \
+                "0.01..0.5, ZG / PNR-LODI, pulse / vortex Mach 0.1..0.5), link PML gradient, " \
+                "1000 steps each (the stated 5000 are out of reach, see the long-run entry), " \
+                "one launch per kernel class over all instances, chunks of 250 steps; wall " \
+                "clock includes admission (host IC + upload) and retirement"
+    out = [b]
+    for rate, count in ((50.0, 500), (5.0, 150)):
+        stream = wl.request_stream(count, rate=rate, seed=0, nmax=2048, smin=100, smax=2000,
+                                   pml_grad="link", nrbc_edges=(0, 0, 0, 0))
+        reqs = [Request(k, t, c, c.steps) for k, (t, c) in enumerate(stream)]
+        sample = {r.rid for r in sorted(reqs, key=lambda r: r.case.nx * r.steps)[:4]}
+        eng = Engine(budget_bytes=100e9, precision="fp32dev", chunk=100, keep_ids=sample)
+        eng.run(reqs)
+        eng.close()
+        sv = summarize(reqs, eng.wall, eng.sites_steps, eng.step_seconds)
+        sv["error"] = _served_error(reqs, sample)
+        sv["what"] = f"Poisson stream {rate:g}/s, {count} requests, bulk log-uniform 64..2048, " \
+                     "PML 8..64, 100..2000 steps (config lengths / 10), link PML gradient, " \
+                     "PNR-LODI on every edge of the NRBC requests, " \
+                     "100 GB admission budget, chunks of 100 steps; latency from arrival to " \
+                     "fields on the host"
+        out.append(sv)
+    return out
 
 
 def main():
@@ -577,9 +624,9 @@ def main():
                    f"{args.window} steps, lbm_moments to pinned host; wall clock"}
 
     # informational sections (single-GPU measurements): rank 0 only, after the timed work
-    batched = serving = variants = None
+    batched = serving = serving_sustainable = variants = None
     if rank == 0 and args.serving:
-        batched, serving = serving_runs(args)
+        batched, serving, serving_sustainable = serving_runs(args)
     if rank == 0 and args.variants:
         variants = variant_runs(args.size, args.window, args.warmup)
     longrun = long_runs(args.size, args.warmup) if rank == 0 and args.long else None
@@ -606,6 +653,7 @@ def main():
             "latency_ms": {"p50": round(statistics.median(per), 5),
                            "p99": round(per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)], 5)},
             "roofline": roof, "step_roofline": step_roof, "fp64": fp64, "batched_fp32": batched, "serving": serving,
+            "serving_sustainable": serving_sustainable,
             "variants_fp32": variants, "long_run_fp32": longrun,
             "e2e": e2e, "cpu_baseline": cpu,
             # per step: k_nrbc_rk4, k_pml_fused, k_gamma, k_bulk (one CUDA-graph replay)

@@ -220,8 +220,10 @@ static cudaError_t dalloc(lbm_ctx* ctx, void** p, size_t bytes) {
   if (e != cudaSuccess) return e;
   ctx->allocs.push_back({base, bytes});
   ctx->alloc_total += bytes;
-  if ((e = cudaMemset(base, kGuardByte, kGuard)) != cudaSuccess) return e;
-  if ((e = cudaMemset(base + kGuard + bytes, kGuardByte, kGuard)) != cudaSuccess) return e;
+  // on the context's stream: creating a context does not wait for other streams' work
+  if ((e = cudaMemsetAsync(base, kGuardByte, kGuard, ctx->st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(base + kGuard + bytes, kGuardByte, kGuard, ctx->st)) != cudaSuccess)
+    return e;
   *p = base + kGuard;
   return cudaSuccess;
 }
@@ -474,21 +476,22 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   };
   for (int k = 0; k < 2; ++k) {
     if (dalloc(ctx, &ctx->f[k], ctx->fbytes) != cudaSuccess) return oom("populations");
-    if (cudaMemset(ctx->f[k], 0, ctx->fbytes) != cudaSuccess) return oom("populations");
+    if (cudaMemsetAsync(ctx->f[k], 0, ctx->fbytes, ctx->st) != cudaSuccess) return oom("populations");
     if (has_pml(g)) {
       if (dalloc(ctx, &ctx->S[k], ctx->sbytes) != cudaSuccess) return oom("PML accumulator");
-      if (cudaMemset(ctx->S[k], 0, ctx->sbytes) != cudaSuccess) return oom("PML accumulator");
+      if (cudaMemsetAsync(ctx->S[k], 0, ctx->sbytes, ctx->st) != cudaSuccess)
+        return oom("PML accumulator");
     }
   }
   if (dalloc(ctx, (void**)&ctx->V, sizeof(double) * 16 * (size_t)g.nb) != cudaSuccess)
     return oom("targets");
   if (dalloc(ctx, (void**)&ctx->Uedge, sizeof(double) * 2 * edge_slots(g)) != cudaSuccess)
     return oom("edges");
-  if (cudaMemset(ctx->V, 0, sizeof(double) * 16 * (size_t)g.nb) != cudaSuccess ||
-      cudaMemset(ctx->Uedge, 0, sizeof(double) * 2 * edge_slots(g)) != cudaSuccess)
+  if (cudaMemsetAsync(ctx->V, 0, sizeof(double) * 16 * (size_t)g.nb, ctx->st) != cudaSuccess ||
+      cudaMemsetAsync(ctx->Uedge, 0, sizeof(double) * 2 * edge_slots(g), ctx->st) != cudaSuccess)
     return oom("targets");
   if (dalloc(ctx, (void**)&ctx->Sedge, sizeof(double) * 2 * source_slots(g)) != cudaSuccess ||
-      cudaMemset(ctx->Sedge, 0, sizeof(double) * 2 * source_slots(g)) != cudaSuccess)
+      cudaMemsetAsync(ctx->Sedge, 0, sizeof(double) * 2 * source_slots(g), ctx->st) != cudaSuccess)
     return oom("PML source");
   if (dalloc(ctx, (void**)&ctx->staging, fieldbytes) != cudaSuccess) return oom("staging");
   if (dalloc(ctx, (void**)&ctx->partials, sizeof(double) * 12 * (size_t)ctx->max_blocks) !=
@@ -564,7 +567,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
     if (ctx->ops.batch_plan(&p0, &p1, 1, 32, 4, &ctx->plan) != cudaSuccess) return oom("plan");
     ctx->dev.plan = &ctx->plan;
   }
-  if (cudaDeviceSynchronize() != cudaSuccess) return oom("device sync");
+  if (cudaStreamSynchronize(ctx->st) != cudaSuccess) return oom("stream sync");
   *out = ctx;
   return LBM_OK;
 }

@@ -238,8 +238,7 @@ __global__ void __launch_bounds__(256) kb_pml_fused(const MemberDev<float>* __re
   extern __shared__ float smem[];
   const int* e = tab + 2 * blockIdx.x;
   const MemberDev<float>& md = mem[e[0]];
-  const Geom g = md.g;
-  pml_fused_tile<S, true>(g, md.c, md.ft, md.A, md.B, md.Sold, md.Snew, md.Uedge_out,
+  pml_fused_tile<S, true>(md.g, md.c, md.ft, md.A, md.B, md.Sold, md.Snew, md.Uedge_out,
                           md.bc.bc == 2 ? 1 : 0, md.flag, md.Sedge_out, md.src_mask, e[1], smem);
 }
 

@@ -185,7 +185,9 @@ __device__ __forceinline__ void pml_fused_tile(const Geom& g, const Consts<float
   else if (!g.py && y == g.Ly - 1) {
     cy0 = 1.5f; cy1 = -2.f; cy2 = 0.5f; oy0 = 0; oy1 = -ew; oy2 = -2 * ew;
   }
-  // the hot loop: BGK + PML term, S^n, store
+  // Appendix PML source at the outermost layer: moments of the selected parts of Omega^PML
+  const bool src = src_mask && outermost(g, x, y);
+  float smom[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < S::Q; ++i) {
     const float eq = eq_dir<S, float, true>(i, m, kc, c);
@@ -199,31 +201,21 @@ __device__ __forceinline__ void pml_fused_tile(const Geom& g, const Consts<float
       if (S::ex(i) != 0) gq += sy * float(S::ex(i)) * (cx0 * q[ox0] + cx1 * q[ox1] + cx2 * q[ox2]);
       if (S::ey(i) != 0) gq += sx * float(S::ey(i)) * (cy0 * q[oy0] + cy1 * q[oy1] + cy2 * q[oy2]);
       out = out - (gq + ssum * fhat + sprod * qn);
+      if (src) {
+        const float part = -(((src_mask & 1) ? gq : 0.f) + ((src_mask & 2) ? ssum * fhat : 0.f) +
+                             ((src_mask & 4) ? sprod * qn : 0.f));
+        smom[0] += part;
+        smom[1] += float(S::ex(i)) * part;
+        smom[2] += float(S::ey(i)) * part;
+        smom[3] += float(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
+      }
     }
     B[(long long)i * g.plane + idx] = out;
   }
-  // Appendix PML source at the outermost layer (a small fraction of the frame): the moments
-  // of the selected parts of Omega^PML, recomputed term by term and summed in FP64 (the sums
-  // cancel heavily), outside the hot loop so that it keeps its registers
-  if (src_mask && in_p && outermost(g, x, y)) {
-    double smom[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = 0; i < S::Q; ++i) {
-      const float fhat = eq_dir<S, float, true>(i, m, kc, c) - c.eqbar[i];
-      const float* q = Qs + i * next + e0;
-      float gq = 0.f;
-      if (S::ex(i) != 0) gq += sy * float(S::ex(i)) * (cx0 * q[ox0] + cx1 * q[ox1] + cx2 * q[ox2]);
-      if (S::ey(i) != 0) gq += sx * float(S::ey(i)) * (cy0 * q[oy0] + cy1 * q[oy1] + cy2 * q[oy2]);
-      const double part = -(((src_mask & 1) ? double(gq) : 0.0) +
-                            ((src_mask & 2) ? double(ssum) * double(fhat) : 0.0) +
-                            ((src_mask & 4) ? double(sprod) * double(q[0]) : 0.0));
-      smom[0] += part;
-      smom[1] += double(S::ex(i)) * part;
-      smom[2] += double(S::ey(i)) * part;
-      smom[3] += double(S::ex(i) * S::ex(i) + S::ey(i) * S::ey(i)) * part;
-    }
-    smom[1] *= double(c.r);
-    smom[2] *= double(c.r);
-    smom[3] *= 0.5 * double(c.r2);
+  if (src) {
+    smom[1] *= c.r;
+    smom[2] *= c.r;
+    smom[3] *= 0.5f * c.r2;
     put_pml_source(g, Sedge, x, y, smom, false);
   }
 }

@@ -116,74 +116,119 @@ class Scheduler:
 
 
 class Engine:
-    def __init__(self, budget_bytes, precision="fp32dev", chunk=100, keep_fields=True):
+    """Continuous batching. Between chunks of steps the loop retires finished and unstable
+    instances and admits queued requests by HBM budget; the initial fields of the requests
+    admitted next are generated on the host and uploaded (on a side stream) while the GPU runs
+    the current chunk, so admission does not leave the GPU idle."""
+
+    def __init__(self, budget_bytes, precision="fp32dev", chunk=100, keep_fields=True,
+                 autotune=False, keep_ids=None, lookahead=16):
+        import torch
         self.precision = precision
         self.chunk = chunk
         self.keep_fields = keep_fields
-        self.sched = Scheduler(budget_bytes)
-        self.batch = Batch()
+        self.keep_ids = keep_ids          # request ids whose fields are kept (None: all)
+        self.autotune = autotune
+        self.tuned = None
+        self.sched = Scheduler(budget_bytes, lookahead)
+        # the batch steps on its own stream and new instances are initialized on another, so
+        # that admission overlaps the running chunk
+        self.stream = torch.cuda.Stream()
+        self.batch = Batch(self.stream)
+        self.side = torch.cuda.Stream()
         self.steps_done = 0
         self.sites_steps = 0
-        self.step_seconds = 0.0   # wall time of the batched stepping alone (launch to sync)
+        self.step_seconds = 0.0   # wall time of the batched stepping (launch to sync)
 
     def _start(self, r, now):
         c = r.case
         s = Solver(c.nx, c.ny, c.W, c.tau, c.sigma_max, c.sigma_power, c.bc, 37, c.nrbc_edges,
-                   c.beta, c.mean, precision=self.precision)
+                   c.beta, c.mean, precision=self.precision, stream=self.side,
+                   pml_grad=getattr(c, "pml_grad", "central"))
         s.init(*c.fields())
         r.solver, r.status, r.admitted, r.remaining = s, "running", now, r.steps
 
     def _finish(self, r, now, status="done"):
-        if status == "done" and self.keep_fields:
-            r.result = r.solver.moments(region="bulk")
+        if status == "done":
+            try:
+                r.solver.sync()
+                if self.keep_fields and (self.keep_ids is None or r.rid in self.keep_ids):
+                    r.result = r.solver.moments(region="bulk")
+            except L.LBMError:
+                status = "unstable"
         r.solver.close()
         r.solver = None
         r.status, r.finished = status, now
         self.sched.release(r)
 
+    def _retire_unstable(self, running, now):
+        for r in list(running):
+            try:
+                r.solver.sync()
+            except L.LBMError:
+                running.remove(r)
+                self._finish(r, now, status="unstable")
+
     def run(self, requests, clock=time.perf_counter):
         """Serve requests (with arrival times) to completion; returns the requests."""
-        import torch
+        main = self.stream
         pending = sorted(requests, key=lambda r: r.arrival)
         for r in pending:
             r.nbytes = estimate_bytes(r.case, self.precision)
         queue, running = [], []
         t0 = clock()
-        while pending or queue or running:
+        inflight = None          # (n, launch time) of the chunk the GPU is running
+        while pending or queue or running or inflight:
             now = clock() - t0
             while pending and pending[0].arrival <= now:
                 queue.append(pending.pop(0))
             for r in [r for r in queue if r.nbytes > self.sched.budget]:
                 queue.remove(r)
                 r.status, r.finished = "rejected", now
+            # admission: host fields + upload on the side stream, overlapping the chunk
             admitted = self.sched.pick(queue)
             for r in admitted:
                 queue.remove(r)
                 self._start(r, now)
-                running.append(r)
+            if inflight is not None:
+                n, t_launch = inflight
+                main.synchronize()
+                self.step_seconds += clock() - t_launch
+                inflight = None
+                if not self._ok:
+                    self._retire_unstable(running, clock() - t0)
+                else:
+                    for r in running:
+                        r.remaining -= n
+                        self.sites_steps += r.solver.Lx * r.solver.Ly * n
+                    for r in [r for r in running if r.remaining == 0]:
+                        running.remove(r)
+                        self._finish(r, clock() - t0)
+            self.side.synchronize()
+            running += admitted
             if not running:
-                if pending:
+                if pending and not queue:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - (clock() - t0))))
                 continue
-            n = min(self.chunk, min(r.remaining for r in running))
             self.batch.set([r.solver for r in running])
-            t_step = clock()
-            if not self.batch.step(n):
-                for r in list(running):
+            if self.autotune and self.tuned is None:
+                k = min(r.remaining for r in running)
+                if k > 8 * 3:
+                    t_launch = clock()
                     try:
-                        r.solver.sync()
+                        self.tuned = self.batch.autotune(steps=2)
+                        for r in running:
+                            r.remaining -= 8 * 3
+                            self.sites_steps += r.solver.Lx * r.solver.Ly * 8 * 3
                     except L.LBMError:
-                        running.remove(r)
-                        self._finish(r, clock() - t0, status="unstable")
-                continue
-            torch.cuda.current_stream().synchronize()
-            self.step_seconds += clock() - t_step
-            for r in running:
-                r.remaining -= n
-                self.sites_steps += (r.case.nx + 2 * r.case.W) * (r.case.ny + 2 * r.case.W) * n
-            for r in [r for r in running if r.remaining == 0]:
-                running.remove(r)
-                self._finish(r, clock() - t0)
+                        self.tuned = ("failed",)
+                        self._retire_unstable(running, clock() - t0)
+                    main.synchronize()
+                    self.step_seconds += clock() - t_launch
+                    continue
+            n = min(self.chunk, min(r.remaining for r in running))
+            inflight = (n, clock())
+            self._ok = self.batch.step(n)
         self.batch.set([])
         self.wall = clock() - t0
         return requests

@@ -210,9 +210,11 @@ def stress_8192(n=8192, W=64, seed=0):
                 nrbc_edges=(0, 1, 0, 0), beta=0.2, mean=(1.0, 0.2, 0.0, 1.0))
 
 
-def batched_sweep(count=256, seed=0, steps=5000):
+def batched_sweep(count=256, seed=0, steps=5000, pml_grad="central", nrbc_edges=(0, 1, 0, 0)):
     """Seeded uneven instances: N ~ U{128..1024}, W ~ U{4..64}, log sigma ~ U[ln .01, ln .5],
-    bc 50/50 zg/nrbc, case 50/50 pulse (A = 1e-3) / vortex (mean Mach ~ U[0.1, 0.5])."""
+    bc 50/50 zg/nrbc, case 50/50 pulse (A = 1e-3) / vortex (mean Mach ~ U[0.1, 0.5]).
+    pml_grad and nrbc_edges (W, E, S, N variants of the characteristic BC) apply to every
+    instance; the draws do not depend on them."""
     rng = np.random.default_rng(seed)
     cases = []
     for k in range(count):
@@ -222,17 +224,21 @@ def batched_sweep(count=256, seed=0, steps=5000):
         bc = "zg" if rng.random() < 0.5 else "nrbc"
         if rng.random() < 0.5:
             cases.append(Case(f"b{k}", n, n, W, 0.8, sig, 3, bc, steps, "pulse",
-                              dict(amp=1e-3, halfwidth=4.0)))
+                              dict(amp=1e-3, halfwidth=4.0), nrbc_edges=tuple(nrbc_edges),
+                              pml_grad=pml_grad))
         else:
             ma = float(rng.uniform(0.1, 0.5))
             cases.append(Case(f"b{k}", n, n, W, 0.8, sig, 3, bc, steps, "vortex",
                               dict(R=20.0, Mv=0.05, mean_u=(ma, 0.0)), beta=ma,
-                              mean=(1.0, ma, 0.0, 1.0)))
+                              mean=(1.0, ma, 0.0, 1.0), nrbc_edges=tuple(nrbc_edges),
+                              pml_grad=pml_grad))
     return cases
 
 
-def request_stream(count=500, rate=50.0, seed=0, nmin=64, nmax=2048, smin=1000, smax=20000):
-    """Poisson request stream: (arrival_time_s, Case). Bulk N log-uniform, W ~ U{8..64}."""
+def request_stream(count=500, rate=50.0, seed=0, nmin=64, nmax=2048, smin=1000, smax=20000,
+                   pml_grad="central", nrbc_edges=(0, 1, 0, 0)):
+    """Poisson request stream: (arrival_time_s, Case). Bulk N log-uniform, W ~ U{8..64}.
+    pml_grad and nrbc_edges apply to every request; the draws do not depend on them."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -243,10 +249,11 @@ def request_stream(count=500, rate=50.0, seed=0, nmin=64, nmax=2048, smin=1000, 
         steps = int(rng.integers(smin, smax + 1))
         if rng.random() < 0.5:
             c = Case(f"r{k}", n, n, W, 0.8, 0.1, 3, "zg", steps, "pulse",
-                     dict(amp=1e-3, halfwidth=4.0))
+                     dict(amp=1e-3, halfwidth=4.0), pml_grad=pml_grad)
         else:
             c = Case(f"r{k}", n, n, W, 0.8, 0.05, 3, "nrbc", steps, "vortex",
                      dict(R=min(20.0, n / 8), Mv=0.05, mean_u=(0.1, 0.0)), beta=0.1,
-                     mean=(1.0, 0.1, 0.0, 1.0))
+                     mean=(1.0, 0.1, 0.0, 1.0), nrbc_edges=tuple(nrbc_edges),
+                     pml_grad=pml_grad)
         out.append((t, c))
     return out
