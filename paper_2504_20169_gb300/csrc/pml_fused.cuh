@@ -1,8 +1,8 @@
 // Single-pass PML frame kernel (FP32 deviation storage): one block per tile of the frame
 // (P + inner ring: the outer Fw / Fe / Fs / Fn layers of F) with a 2-node halo.
 //
-//  A  every owned node and every node of tile + halo that carries Q (distance <= W along a
-//     PML axis) pulls its populations and takes its moments; the latter store
+//  A  every owned node and every halo node phase C reads that carries Q (distance <= W along
+//     a PML axis) pulls its populations and takes its moments; the latter store
 //     Q_i = S_i^(n-1) + f_hat_i^n / 2 for all i in shared memory (trapezoidal accumulator,
 //     Eq. PMLQ; f_hat = f_eq - f_eq_bar, Eq. decomp-NJ);
 //  C  every owned node pulls again (cache hits), collides with BGK (moments kept from A),
@@ -110,12 +110,21 @@ __device__ __forceinline__ void pml_fused_tile(const Geom& g, const Consts<float
   // ---- A: Q on tile + halo; equilibria and moments of the owned nodes kept for phase C
   for (int e = tid; e < next; e += blockDim.x) {
     const int ex = e % ew, ey = e / ew;
+    const int tx = ex - 2, ty = ey - 2;
+    // halo nodes phase C never reads: the corners (the differences are per axis), and the
+    // second halo column / row unless the tile's edge column / row is an outermost layer of F
+    // whose one-sided stencil (Eq. FD-dx-bw) reaches two nodes inward
+    const bool xin = tx >= 0 && tx < tw, yin = ty >= 0 && ty < th;
+    if (!xin && !yin) continue;
+    if (tx == -2 && x0 != g.Lx - 1) continue;
+    if (tx == tw + 1 && x0 + tw - 1 != 0) continue;
+    if (ty == -2 && (g.py || y0 != g.Ly - 1)) continue;
+    if (ty == th + 1 && (g.py || y0 + th - 1 != 0)) continue;
     const int x = x0 - 2 + ex;
     int y = y0 - 2 + ey;
     if (g.py) y = (y + g.Ly) % g.Ly;   // halo rows wrap along a periodic y axis
     if (x < 0 || y < 0 || x >= g.Lx || y >= g.Ly) continue;
-    const int tx = ex - 2, ty = ey - 2;
-    const int own = (tx >= 0 && ty >= 0 && tx < tw && ty < th) ? ty * tw + tx : -1;
+    const int own = (xin && yin) ? ty * tw + tx : -1;
     // frame nodes farther out than the PML along neither axis (a frame depth set by M
     // where an axis has no PML) still need their moments for phase C
     const bool hq = pml_node<float>(g, x, y).has_q;
