@@ -555,7 +555,7 @@ lbm_status lbm_create(const lbm_grid* grid, lbm_stencil stencil, double tau, int
   d.cd.sigma_max = sg.sigma_max; d.cd.power = sg.power; d.cd.split = sg.split;
   d.cf.r = (float)ctx->r; d.cf.r2 = (float)(ctx->r * ctx->r); d.cf.omega = (float)ctx->omega;
   d.cf.sigma_max = (float)sg.sigma_max; d.cf.power = sg.power; d.cf.split = sg.split;
-  if (ctx->ops.prepare() != cudaSuccess) return oom("kernel attributes");
+  if (ctx->ops.prepare(ctx->w) != cudaSuccess) return oom("kernel attributes");
   {
     // the context's one-member plan, for buffer parity 0 and 1
     set_roles(ctx, 0, 0);

@@ -209,6 +209,30 @@ __host__ __device__ inline Macro<Real> moments(const Real (&p)[S::Q], const Cons
   return m;
 }
 
+// Quadrature weights in constant memory, one table per stencil and precision (filled once per
+// device when the first context is created there): with a direction index known at compile
+// time, a kernel reads its weight as an instruction operand instead of a load. Host code (the
+// mean equilibrium) reads the context's constants.
+static __constant__ double kw37d[37], kw17d[17], kw9d[9];
+static __constant__ float kw37f[37], kw17f[17], kw9f[9];
+
+template <class S, class Real>
+__host__ __device__ inline Real weight(const Consts<Real>& c, int i) {
+#ifdef __CUDA_ARCH__
+  if constexpr (sizeof(Real) == 8) {
+    if constexpr (S::Q == 37) return kw37d[i];
+    else if constexpr (S::Q == 17) return kw17d[i];
+    else return kw9d[i];
+  } else {
+    if constexpr (S::Q == 37) return kw37f[i];
+    else if constexpr (S::Q == 17) return kw17f[i];
+    else return kw9f[i];
+  }
+#else
+  return c.w[i];
+#endif
+}
+
 // Site coefficients of the equilibrium polynomial in a = xi . u (Eqs. feq-2/3/4):
 //   P(a) = C0 + C1 a + C2 a^2 + C3 a^3 + C4 a^4,   C0 = k00 + c2 (k01 + c2 k02),
 //   C1 = k10 + c2 k11, C2 = k20 + c2 k21, C3 = 1/6 (order >= 3), C4 = 1/24 (order 4),
@@ -262,8 +286,8 @@ __host__ __device__ inline Real eq_dir(int i, const Macro<Real>& m, const EqCoef
     poly = poly + a * C34;
   }
   const Real Pm1 = C0m + a * (C1 + a * poly);  // P - 1
-  if (DEV) return c.w[i] * (m.rho * Pm1 + m.drho);
-  return c.w[i] * m.rho * (Real(1) + Pm1);
+  if (DEV) return weight<S, Real>(c, i) * (m.rho * Pm1 + m.drho);
+  return weight<S, Real>(c, i) * m.rho * (Real(1) + Pm1);
 }
 
 // Same, for all directions at once using the +/- pairing: E(a) = C0 + a^2 (C2 + a^2 C4),
@@ -282,8 +306,8 @@ __device__ inline void collide_bgk(Real (&p)[S::Q], const Macro<Real>& m,
     const Real C0m = k.k00m + c2 * (k.k01 + c2 * k.k02);
     const Real C1 = k.k10 + c2 * k.k11;
     const Real C2 = k.k20 + c2 * k.k21;
-    const Real wr = om * c.w[i0] * m.rho;     // omega w rho (a shell shares w)
-    const Real wd = om * c.w[i0] * m.drho;
+    const Real wr = om * weight<S, Real>(c, i0) * m.rho;     // omega w rho (a shell shares w)
+    const Real wd = om * weight<S, Real>(c, i0) * m.drho;
     const Real keep = Real(1) - om;
     if (n == 1) {
       const Real eq = DEV ? (wr * C0m + wd) : (wr + wr * C0m);

@@ -82,7 +82,8 @@ struct BatchPlan {
 };
 
 struct OpsTable {
-  cudaError_t (*prepare)();   // kernel attributes on the current device
+  cudaError_t (*prepare)(const double* w);   // kernel attributes and the quadrature weights
+                                             // (constant memory) on the current device
   cudaError_t (*step)(const Dev&, bool stream);
   cudaError_t (*init_eq)(const Dev&, const double*, const double*, const double*, const double*);
   cudaError_t (*fields)(const Dev&, const void* src, bool stream, int region, double* const o[4],

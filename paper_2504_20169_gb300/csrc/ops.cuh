@@ -5,6 +5,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "lbm_device.cuh"
@@ -450,7 +451,28 @@ struct Ops {
   }
 
   // per-device kernel attributes, set once for every context on the context's device
-  static cudaError_t prepare() {
+  static cudaError_t prepare(const double* w) {
+    // weights in constant memory, once per device (the values never change)
+    {
+      static std::mutex mu;
+      static bool done[64] = {};
+      int dev = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e != cudaSuccess) return e;
+      std::lock_guard<std::mutex> lock(mu);
+      if (dev < 0 || dev >= 64 || !done[dev]) {
+        Real wr[S::Q];
+        for (int i = 0; i < S::Q; ++i) wr[i] = Real(w[i]);
+        const void* sym;
+        if constexpr (sizeof(Real) == 8)
+          sym = S::Q == 37 ? (const void*)&kw37d : S::Q == 17 ? (const void*)&kw17d : (const void*)&kw9d;
+        else
+          sym = S::Q == 37 ? (const void*)&kw37f : S::Q == 17 ? (const void*)&kw17f : (const void*)&kw9f;
+        e = cudaMemcpyToSymbol(sym, wr, sizeof(wr));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) done[dev] = true;
+      }
+    }
     if constexpr (DEV) {
       cudaError_t e = cudaFuncSetAttribute(k_pml_fused<S, true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

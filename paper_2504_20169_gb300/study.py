@@ -201,12 +201,17 @@ def run_bench_workload(steps=200, sample=20, precision="fp32dev", n=2048, W=32):
             f = ref.moments(region="F", device=True)
             refs.append([t[pad:pad + n, pad:pad + n].contiguous() for t in f])
     mean = (1.0, 0.3, 0.0, 1.0)
-    cases = [("ZG", "zg", 0, (0, 0, 0, 0)), ("ZG + PML", "zg", W, (0, 0, 0, 0)),
-             ("CBC(A)", "nrbc", 0, (0, 1, 0, 0)), ("CBC(A) + PML (benchmark)", "nrbc", W, (0, 1, 0, 0))]
+    cases = [("ZG", "zg", 0, (0, 0, 0, 0), "central"),
+             ("ZG + PML", "zg", W, (0, 0, 0, 0), "central"),
+             ("ZG + PML (link gradient)", "zg", W, (0, 0, 0, 0), "link"),
+             ("CBC(A)", "nrbc", 0, (0, 1, 0, 0), "central"),
+             ("CBC(A) + PML (benchmark)", "nrbc", W, (0, 1, 0, 0), "central"),
+             ("CBC(A) + PML (link gradient)", "nrbc", W, (0, 1, 0, 0), "link"),
+             ("PNR + PML (link gradient)", "nrbc", W, (0, 0, 0, 0), "link")]
     results = []
-    for label, bc, w, edges in cases:
+    for label, bc, w, edges, grad in cases:
         with Solver(n, n, w, tau, 0.1 if w else 0.0, 3, bc, 37, edges, 0.3, mean,
-                    precision=precision) as s:
+                    precision=precision, pml_grad=grad) as s:
             s.init(*wl.isentropic_vortex(n, n, w, **vort))
             e = {"rho": [], "ux": [], "T": []}
             status = "ok"
@@ -287,7 +292,9 @@ def main():
         print("| precision | BC | W | e_bar rho | e_bar u_x | e_bar T | rms rel. error rho at end |")
         print("|---|---|---|---|---|---|---|")
         for prec in ("fp32dev", "fp64"):
-            meta, results = run_bench_workload(steps=a.steps or 200, precision=prec)
+            st = a.steps or 200
+            meta, results = run_bench_workload(steps=st, precision=prec,
+                                               sample=20 if st <= 400 else 50)
             print(json.dumps(meta))
             for r in results:
                 eb = r["ebar"]

@@ -302,3 +302,28 @@ def test_unphysical_state_is_reported():
         with pytest.raises(LBMError) as ei:
             s.sync()
         assert "UNSTABLE" in str(ei.value)
+
+
+@pytest.mark.parametrize("grad", ["central", "link"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+def test_parity_benchmark_parameters_over_the_benchmark_window(precision, grad):
+    """The benchmark configuration's physics and boundary (tau 0.55, cubic sigma_max 0.1,
+    W 32, east CBC relax with beta 0.3, PNR-LODI elsewhere, isentropic vortex in a Mach 0.3
+    flow) on a 128^2 bulk (about half of F is PML), for the 150 steps of one benchmark window.
+    Known FP32 gap with the printed gradient: its growing PML modes amplify the FP32 rounding
+    (they show in the FP64 path too, at 5e-13), and u_y reaches 1.2e-5 in the velocity measure,
+    above the 1e-5 of the other cases; bounded at 3e-5 so that a regression still fails. With
+    the link-integrated gradient the same case is held to the usual bounds."""
+    c = wl.vortex_2048(n=128, W=32)
+    kw = case_kwargs(nx=c.nx, ny=c.ny, W=c.W, tau=c.tau, sigma_max=c.sigma_max,
+                     sigma_power=c.sigma_power, bc=c.bc, nrbc_edges=c.nrbc_edges, beta=c.beta,
+                     mean=c.mean, pml_grad=grad)
+    fields = wl.isentropic_vortex(c.nx, c.ny, c.W, R=8.0, Mv=0.05, mean_u=(0.3, 0.0))
+    if precision == "fp32dev" and grad == "central":
+        ora, _ = run_oracle(kw, fields, 150)
+        full, pert = field_errors(run_gpu(kw, fields, 150, precision), ora)
+        print(f"{precision} full={['%.2e' % e for e in full]} pert={['%.2e' % e for e in pert]}")
+        assert max(full[0], full[3]) < 1e-5 and max(full[1], full[2]) < 3e-5, full
+        assert max(pert) < 0.1, pert
+        return
+    check(kw, fields, 150, precision, tag=grad + " ")
