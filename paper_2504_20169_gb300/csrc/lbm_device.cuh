@@ -446,11 +446,14 @@ __device__ inline bool outermost(const Geom& g, int x, int y) {
 // Frame, phase 1: BGK plus, on P and its inner ring, the trapezoidal accumulator
 // S = Q + f_hat / 2 (Eq. PMLQ: Q^n = S^(n-1) + f_hat^n / 2, S^n = S^(n-1) + f_hat^n), and on P
 // the local part -((sigma_x + sigma_y) f_hat + sigma_x sigma_y Q) of Eq. (pml-general)
-// (-sigma (2 f_hat + sigma Q) of Eq. PMLCOLL when sigma_x = sigma_y).
+// (-sigma (2 f_hat + sigma Q) of Eq. PMLCOLL when sigma_x = sigma_y). With the link gradient
+// the node also stores Q^n in place of S^(n-1) (no kernel of the step reads S^(n-1) after its
+// own node's phase 1; the next step writes S^(n+1) there) and adds its own share
+// +sigma Q_i(x) of the link difference, so phase 2 gathers one value per direction.
 template <class S, class Real, bool DEV, bool STREAM>
 __device__ __forceinline__ void frame1_node(const Geom& g, const Consts<Real>& c,
                                             const Real* __restrict__ A, Real* __restrict__ B,
-                                            const Real* __restrict__ Sold,
+                                            Real* __restrict__ Sold,
                                             Real* __restrict__ Snew, double* Uedge,
                                             int save_edges, int* flag, double* Sedge,
                                             int src_mask, int fi) {
@@ -476,18 +479,28 @@ __device__ __forceinline__ void frame1_node(const Geom& g, const Consts<Real>& c
   const bool src = src_mask && outermost(g, x, y);
   double smom[4] = {0.0, 0.0, 0.0, 0.0};   // FP64 sums (cancellation)
   if (has_q) {
-    // all accumulator loads in flight before any store
+    // FP32: all accumulator loads in flight before any store (the FP64 build has no registers
+    // to spare for them next to its populations)
+    constexpr bool kHoist = sizeof(Real) == 4;
     Real so[S::Q];
+    if (kHoist) {
 #pragma unroll
-    for (int i = 0; i < S::Q; ++i) so[i] = __ldg(Sold + (long long)i * g.Sp + fi);
+      for (int i = 0; i < S::Q; ++i) so[i] = Sold[(long long)i * g.Sp + fi];
+    }
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       const Real eq = eq_dir<S, Real, DEV>(i, m, k, c);
       const Real fhat = eq - c.eqbar[i];
-      const Real q = so[i] + Real(0.5) * fhat;
-      Snew[(long long)i * g.Sp + fi] = so[i] + fhat;
+      const Real s0 = kHoist ? so[i] : Sold[(long long)i * g.Sp + fi];
+      const Real q = s0 + Real(0.5) * fhat;
+      Snew[(long long)i * g.Sp + fi] = s0 + fhat;
+      if (g.link) Sold[(long long)i * g.Sp + fi] = q;   // Q^n over S^(n-1), gathered by phase 2
       Real out = p[i] + c.omega * (eq - p[i]);
-      if (in_p) out = out - (ssum * fhat + sprod * q);
+      if (in_p) {
+        out = out - (ssum * fhat + sprod * q);
+        // link mode: the node's own share +sigma Q_i(x) of -sigma (Q_i(x + e_i) - Q_i(x))
+        if (g.link && (S::ex(i) != 0 || S::ey(i) != 0)) out = out + sx * q;
+      }
       B[(long long)i * g.plane + idx] = out;
       if (src && in_p) {
         const double part = -(((src_mask & 2) ? double(ssum) * double(fhat) : 0.0) +
@@ -514,7 +527,7 @@ __device__ __forceinline__ void frame1_node(const Geom& g, const Consts<Real>& c
 
 template <class S, class Real, bool DEV, bool STREAM>
 __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Real* __restrict__ A,
-                                                Real* __restrict__ B, const Real* __restrict__ Sold,
+                                                Real* __restrict__ B, Real* __restrict__ Sold,
                                                 Real* __restrict__ Snew, double* Uedge, int save_edges,
                                                 int* flag, double* Sedge, int src_mask) {
   frame1_node<S, Real, DEV, STREAM>(g, c, A, B, Sold, Snew, Uedge, save_edges, flag, Sedge,
@@ -523,7 +536,8 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
 
 // Frame, phase 2 (PML nodes): subtract sigma_y c_ix dQ_i/dx + sigma_x c_iy dQ_i/dy (sigma
 // e_i . grad Q_i when sigma_x = sigma_y) with Q = (S^(n-1) + S^n) / 2,
-// Eq. (FD-dx-center) per axis, Eq. (FD-dx-bw) along the outward normal at the outermost layer.
+// Eq. (FD-dx-center) per axis, Eq. (FD-dx-bw) along the outward normal at the outermost layer;
+// with the link gradient, the neighbour's share of the link difference (Q^n read in place).
 template <class S, class Real>
 __device__ __forceinline__ void frame2_node(const Geom& g, const Consts<Real>& c,
                                             Real* __restrict__ B, const Real* __restrict__ Sold,
@@ -537,23 +551,43 @@ __device__ __forceinline__ void frame2_node(const Geom& g, const Consts<Real>& c
   Real sx, sy;
   pml_sigmas(c, pn, sx, sy);
   if (g.link) {
-    // link mode: sigma (Q_i(x + e_i) - Q_i(x)), the integral of sigma c_i . grad Q_i along the
-    // link the population travels (sigma_x = sigma_y); Q = (S^(n-1) + S^n) / 2 on the frame
-    // and on the boundary nodes outside F
+    // link mode: the remaining -sigma Q_i(x + e_i) of -sigma (Q_i(x + e_i) - Q_i(x)), the
+    // integral of sigma c_i . grad Q_i along the link the population travels (sigma_x =
+    // sigma_y); phase 1 added +sigma Q_i(x), and Q^n sits in the S^(n-1) slots of the frame and
+    // of the boundary nodes outside F, where phase 1 and the band kernel stored it
     const long long idx = gindex(g, x, y);
     const bool src = (src_mask & 1) && outermost(g, x, y);   // Appendix term I
+    // a node whose whole stencil lies in its own band finds a neighbour's slot at a linear
+    // offset (row length rl) from its own; other nodes use q_slot
+    constexpr int R = S::M;
+    int rl = 0;
+    if (y < g.Fs) {
+      if (x >= R && x < g.Lx - R && y >= R && y + R < g.Fs) rl = g.Lx;
+    } else if (y >= g.Ly - g.Fn) {
+      if (x >= R && x < g.Lx - R && y - R >= g.Ly - g.Fn && y + R < g.Ly) rl = g.Lx;
+    } else if (x < g.Fw) {
+      if (x >= R && x + R < g.Fw && y - R >= g.Fs && y + R < g.Ly - g.Fn) rl = g.Fw;
+    } else {
+      if (x - R >= g.Lx - g.Fe && x + R < g.Lx && y - R >= g.Fs && y + R < g.Ly - g.Fn) rl = g.Fe;
+    }
     double smom[4] = {0.0, 0.0, 0.0, 0.0};   // FP64 sums (cancellation)
+    // every gather in flight before the first update of B
+    Real qg[S::Q];
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       if (S::ex(i) == 0 && S::ey(i) == 0) continue;
-      const Real* so = Sold + (long long)i * g.Sp;
-      const Real* sn = Snew + (long long)i * g.Sp;
-      const int nb = q_slot(g, x + S::ex(i), y + S::ey(i));
-      const Real gq = sx * ((__ldg(so + nb) + __ldg(sn + nb)) - (__ldg(so + fi) + __ldg(sn + fi)));
+      const int nb = rl ? fi + S::ey(i) * rl + S::ex(i) : q_slot(g, x + S::ex(i), y + S::ey(i));
+      qg[i] = __ldg(Sold + (long long)i * g.Sp + nb);
+    }
+#pragma unroll
+    for (int i = 0; i < S::Q; ++i) {
+      if (S::ex(i) == 0 && S::ey(i) == 0) continue;
+      const Real* sq = Sold + (long long)i * g.Sp;
+      const Real qn = qg[i];
       Real* b = B + (long long)i * g.plane + idx;
-      *b = *b - Real(0.5) * gq;
+      *b = *b - sx * qn;
       if (src) {
-        const double part = -0.5 * double(gq);
+        const double part = -double(sx) * (double(qn) - double(__ldg(sq + fi)));
         smom[0] += part;
         smom[1] += double(S::ex(i)) * part;
         smom[2] += double(S::ey(i)) * part;
@@ -678,13 +712,14 @@ __device__ inline int q_slot(const Geom& g, int x, int y) {
 // f_eq(U_tgt) + (1 - omega) f_neq(x_f); the corner blocks use the zero-gradient copy.
 // Periodic: the post-collision value of the periodic image.
 // Link mode with a PML (Sold != nullptr): the node also advances its accumulator
-// S^n = S^(n-1) + f_hat^n (slot frame_n + t) from the moments of its pre-collision state.
+// S^n = S^(n-1) + f_hat^n (slot frame_n + t) from the moments of its pre-collision state, and
+// stores Q^n = S^(n-1) + f_hat^n / 2 in place of S^(n-1) for the frame's phase 2.
 template <class S, class Real, bool DEV, bool STREAM>
 __device__ __forceinline__ void gamma_node(const Geom& g, const Consts<Real>& c,
                                            const BcParams& bc, const Real* __restrict__ A,
                                            Real* __restrict__ B,
                                            const double* __restrict__ Vtgt,
-                                           const Real* __restrict__ Sold,
+                                           Real* __restrict__ Sold,
                                            Real* __restrict__ Snew, int t) {
   if (t >= g.ngamma) return;
   int x, y;
@@ -725,6 +760,13 @@ __device__ __forceinline__ void gamma_node(const Geom& g, const Consts<Real>& c,
     const EqCoef<Real> kf = eq_coef<S::ORDER, Real>(m);
     const EqCoef<Real> kt = eq_coef<S::ORDER, Real>(mt);
     const Real keep = Real(1) - c.omega;
+    // FP32: accumulator loads in flight before any store (FP64 has no registers to spare)
+    constexpr bool kHoist = sizeof(Real) == 4;
+    Real so[S::Q];
+    if (kHoist && Sold) {
+#pragma unroll
+      for (int i = 0; i < S::Q; ++i) so[i] = Sold[(long long)i * g.Sp + g.frame_n + t];
+    }
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       const Real neq = p[i] - eq_dir<S, Real, DEV>(i, m, kf, c);
@@ -732,17 +774,28 @@ __device__ __forceinline__ void gamma_node(const Geom& g, const Consts<Real>& c,
       B[(long long)i * g.plane + dst] = eqt + keep * neq;
       if (Sold) {
         const long long k = (long long)i * g.Sp + g.frame_n + t;
-        Snew[k] = Sold[k] + (eqt - c.eqbar[i]);
+        const Real s0 = kHoist ? so[i] : Sold[k], fh = eqt - c.eqbar[i];
+        Snew[k] = s0 + fh;
+        Sold[k] = s0 + Real(0.5) * fh;   // Q^n in place, gathered by the frame's phase 2
       }
     }
     return;
   }
   if (Sold) {
     const EqCoef<Real> kf = eq_coef<S::ORDER, Real>(m);
+    constexpr bool kHoist = sizeof(Real) == 4;   // as above
+    Real so[S::Q];
+    if (kHoist) {
+#pragma unroll
+      for (int i = 0; i < S::Q; ++i) so[i] = Sold[(long long)i * g.Sp + g.frame_n + t];
+    }
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       const long long k = (long long)i * g.Sp + g.frame_n + t;
-      Snew[k] = Sold[k] + (eq_dir<S, Real, DEV>(i, m, kf, c) - c.eqbar[i]);
+      const Real s0 = kHoist ? so[i] : Sold[k];
+      const Real fh = eq_dir<S, Real, DEV>(i, m, kf, c) - c.eqbar[i];
+      Snew[k] = s0 + fh;
+      Sold[k] = s0 + Real(0.5) * fh;   // Q^n in place, gathered by the frame's phase 2
     }
   }
   collide_bgk<S, Real, DEV>(p, m, c);
@@ -754,7 +807,7 @@ template <class S, class Real, bool DEV, bool STREAM>
 __global__ void __launch_bounds__(128) k_gamma(Geom g, Consts<Real> c, BcParams bc,
                                                const Real* __restrict__ A, Real* __restrict__ B,
                                                const double* __restrict__ Vtgt,
-                                               const Real* __restrict__ Sold,
+                                               Real* __restrict__ Sold,
                                                Real* __restrict__ Snew) {
   gamma_node<S, Real, DEV, STREAM>(g, c, bc, A, B, Vtgt, Sold, Snew,
                                    blockIdx.x * blockDim.x + threadIdx.x);

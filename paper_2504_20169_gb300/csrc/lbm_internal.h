@@ -16,7 +16,7 @@ struct Dev {
   Consts<float> cf;
   const void* A;     // post-collision populations of the current level (read)
   void* B;           // next level (written)
-  const void* Sold;  // PML accumulator S^(n-1)
+  void* Sold;        // PML accumulator S^(n-1) (link mode: Q^n in place during the step)
   void* Snew;        // S^n
   double* Vtgt;      // characteristic targets U_tgt [4][nb]
   double* Va;        // Runge-Kutta stage buffers [4][nb]

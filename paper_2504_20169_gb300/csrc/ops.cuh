@@ -212,7 +212,7 @@ struct MemberDev {
   FrameTiles ft;
   const Real* A;
   Real* B;
-  const Real* Sold;
+  Real* Sold;
   Real* Snew;
   double* Vtgt;
   double* Uedge_out;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(128) kb_frame1(const MemberDev<Real>* __restri
 }
 
 template <class S, class Real>
-__global__ void __launch_bounds__(128) kb_frame2(const MemberDev<Real>* __restrict__ mem,
+__global__ void __launch_bounds__(128, sizeof(Real) == 4 ? 4 : 2) kb_frame2(const MemberDev<Real>* __restrict__ mem,
                                                  const int* __restrict__ tab) {
   const int* e = tab + 2 * blockIdx.x;
   const MemberDev<Real>& md = mem[e[0]];
@@ -361,13 +361,13 @@ struct Ops {
     }
     if (!fused && !pl)
       k_frame1<S, Real, DEV, STREAM><<<(g.frame_n + 127) / 128, 128, 0, fs>>>(
-          g, c, A, B, static_cast<const Real*>(d.Sold), static_cast<Real*>(d.Snew), d.Uedge_out,
+          g, c, A, B, static_cast<Real*>(d.Sold), static_cast<Real*>(d.Snew), d.Uedge_out,
           d.bc.bc == 2 ? 1 : 0, d.flag, d.Sedge_out, src_mask);
     if (!pl) mark(5, fs);
     auto band = [&]() {
       mark(8, bs);
       k_gamma<S, Real, DEV, STREAM><<<(g.ngamma + 127) / 128, 128, 0, bs>>>(
-          g, c, d.bc, A, B, d.Vtgt, link ? static_cast<const Real*>(d.Sold) : nullptr,
+          g, c, d.bc, A, B, d.Vtgt, link ? static_cast<Real*>(d.Sold) : nullptr,
           link ? static_cast<Real*>(d.Snew) : nullptr);
       mark(9, bs);
     };
@@ -417,10 +417,10 @@ struct Ops {
     dim3 grid((g.Lx + 127) / 128, g.Ly);
     k_init_eq<S, Real, DEV><<<grid, 128, 0, d.st>>>(g, consts(d), rho, ux, uy, T,
                                                    static_cast<Real*>(const_cast<void*>(d.A)),
-                                                   static_cast<Real*>(const_cast<void*>(d.Sold)));
+                                                   static_cast<Real*>(d.Sold));
     if (g.link && has_pml(g))
       k_init_gamma_s<S, Real, DEV><<<(g.ngamma + 127) / 128, 128, 0, d.st>>>(
-          g, consts(d), rho, ux, uy, T, static_cast<Real*>(const_cast<void*>(d.Sold)));
+          g, consts(d), rho, ux, uy, T, static_cast<Real*>(d.Sold));
     return cudaGetLastError();
   }
 
@@ -497,7 +497,7 @@ struct Ops {
     m.ft = make_frame_tiles(d.g, 256);
     m.A = static_cast<const Real*>(d.A);
     m.B = static_cast<Real*>(d.B);
-    m.Sold = static_cast<const Real*>(d.Sold);
+    m.Sold = static_cast<Real*>(d.Sold);
     m.Snew = static_cast<Real*>(d.Snew);
     m.Vtgt = d.Vtgt;
     m.Uedge_out = d.Uedge_out;
