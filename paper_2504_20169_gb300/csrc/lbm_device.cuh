@@ -571,13 +571,15 @@ __device__ __forceinline__ void frame2_node(const Geom& g, const Consts<Real>& c
       if (x - R >= g.Lx - g.Fe && x + R < g.Lx && y - R >= g.Fs && y + R < g.Ly - g.Fn) rl = g.Fe;
     }
     double smom[4] = {0.0, 0.0, 0.0, 0.0};   // FP64 sums (cancellation)
-    // every gather in flight before the first update of B
-    Real qg[S::Q];
+    // every gather (and in FP32 every load of B) in flight before the first update of B
+    constexpr bool kHoistB = sizeof(Real) == 4;
+    Real qg[S::Q], bg[S::Q];
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       if (S::ex(i) == 0 && S::ey(i) == 0) continue;
       const int nb = rl ? fi + S::ey(i) * rl + S::ex(i) : q_slot(g, x + S::ex(i), y + S::ey(i));
       qg[i] = __ldg(Sold + (long long)i * g.Sp + nb);
+      if (kHoistB) bg[i] = B[(long long)i * g.plane + idx];
     }
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
@@ -585,7 +587,7 @@ __device__ __forceinline__ void frame2_node(const Geom& g, const Consts<Real>& c
       const Real* sq = Sold + (long long)i * g.Sp;
       const Real qn = qg[i];
       Real* b = B + (long long)i * g.plane + idx;
-      *b = *b - sx * qn;
+      *b = (kHoistB ? bg[i] : *b) - sx * qn;
       if (src) {
         const double part = -double(sx) * (double(qn) - double(__ldg(sq + fi)));
         smom[0] += part;

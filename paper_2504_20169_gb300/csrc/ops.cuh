@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(128) kb_frame1(const MemberDev<Real>* __restri
 }
 
 template <class S, class Real>
-__global__ void __launch_bounds__(128, sizeof(Real) == 4 ? 4 : 2) kb_frame2(const MemberDev<Real>* __restrict__ mem,
+__global__ void __launch_bounds__(128, sizeof(Real) == 4 ? 3 : 2) kb_frame2(const MemberDev<Real>* __restrict__ mem,
                                                  const int* __restrict__ tab) {
   const int* e = tab + 2 * blockIdx.x;
   const MemberDev<Real>& md = mem[e[0]];
