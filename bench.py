@@ -20,6 +20,7 @@ scaling is weak and there is no data-path collective.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -58,6 +59,10 @@ def parse():
                     help="also run the batched sweep and the serving stream (0 skips)")
     ap.add_argument("--size", type=int, default=2048,
                     help="bulk edge (2048 = the workload; smaller sizes for profiler captures)")
+    ap.add_argument("--pml-grad", default="central", choices=("central", "link"),
+                    help="PML gradient of the headline workload: the printed differences (the "
+                         "workload as stated) or the link-integrated option (its kernels' "
+                         "timings and profiles)")
     return ap.parse_args()
 
 
@@ -251,7 +256,7 @@ def timed_run(Solver, c, fields, precision, steps, warmup, dev, window, prof_ste
     events around every kernel class (the interior kernel's live duration)."""
     import torch
     s = Solver(c.nx, c.ny, c.W, c.tau, c.sigma_max, c.sigma_power, c.bc, 37, c.nrbc_edges,
-               c.beta, c.mean, precision=precision)
+               c.beta, c.mean, precision=precision, pml_grad=c.pml_grad)
     s.init(*fields)
     s.step(warmup)
     s.sync()
@@ -509,6 +514,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     c = wl.vortex_2048(n=args.size)
+    if args.pml_grad != c.pml_grad:
+        c = dataclasses.replace(c, pml_grad=args.pml_grad)
     fields = c.fields()
     Lx = c.nx + 2 * c.W
     sites = Lx * Lx
@@ -582,7 +589,7 @@ def main():
         res = {}
         for prec in ("fp32dev", "fp64"):
             with Solver(c.nx, c.ny, c.W, c.tau, c.sigma_max, c.sigma_power, c.bc, 37,
-                        c.nrbc_edges, c.beta, c.mean, precision=prec) as s:
+                        c.nrbc_edges, c.beta, c.mean, precision=prec, pml_grad=c.pml_grad) as s:
                 s.init(*fields)
                 s.step(args.window)
                 res[prec] = (s.moments(region="F", device=True),
@@ -600,7 +607,7 @@ def main():
     pin = [torch.from_numpy(np.ascontiguousarray(f)).pin_memory() for f in fields]
     outs = [torch.empty((Lx, Lx), dtype=torch.float64).pin_memory() for _ in range(4)]
     s = Solver(c.nx, c.ny, c.W, c.tau, c.sigma_max, c.sigma_power, c.bc, 37, c.nrbc_edges,
-               c.beta, c.mean, precision="fp32dev")
+               c.beta, c.mean, precision="fp32dev", pml_grad=c.pml_grad)
     import ctypes as C
     from paper_2504_20169_gb300 import _lib as L
     barrier()
@@ -641,8 +648,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.size == 2048 else f"vortex{args.size}_w32_nrbc_d2q37",
-                       "bulk": [c.nx, c.ny], "pml_width": c.W,
+            "config": {"workload": (WORKLOAD if args.size == 2048 else f"vortex{args.size}_w32_nrbc_d2q37")
+                       + ("" if c.pml_grad == "central" else "_link_gradient"),
+                       "bulk": [c.nx, c.ny], "pml_width": c.W, "pml_gradient": c.pml_grad,
                        "sigma": "cubic, sigma_max 0.1", "bc": "E: CBC relax beta 0.3; W,S,N: PNR-LODI",
                        "tau": c.tau, "stencil": "D2Q37", "storage": "FP32 deviation from rest weights",
                        "fluid_nodes_per_step": sites, "working_set_bytes": step_bytes,
@@ -656,8 +664,10 @@ def main():
             "serving_sustainable": serving_sustainable,
             "variants_fp32": variants, "long_run_fp32": longrun,
             "e2e": e2e, "cpu_baseline": cpu,
-            # per step: k_nrbc_rk4, k_pml_fused, k_gamma, k_bulk (one CUDA-graph replay)
-            "gpu_launches": args.steps * (4 if c.bc == "nrbc" else 3), "clocks": ck,
+            # per step: k_nrbc_rk4, k_pml_fused, k_gamma, k_bulk (one CUDA-graph replay); the
+            # link gradient runs the frame as two kernels
+            "gpu_launches": args.steps * ((4 if c.bc == "nrbc" else 3) + (c.pml_grad == "link")),
+            "clocks": ck,
             "also": {"mlups_bulk_only": round(value * c.nx * c.ny / sites, 1),
                      "mlups_over_G": round(value * (Lx + 6) * (Lx + 6) / sites, 1),
                      "note": "bulk-only counts the PML as overhead (the paper's view); over G "
