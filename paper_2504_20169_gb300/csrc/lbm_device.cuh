@@ -443,6 +443,16 @@ __device__ inline bool outermost(const Geom& g, int x, int y) {
   return x == 0 || x == g.Lx - 1 || (!g.py && (y == 0 || y == g.Ly - 1));
 }
 
+// 4-byte asynchronous global -> shared copy (cp.async) and the wait for all of this thread's
+// copies.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // Frame, phase 1: BGK plus, on P and its inner ring, the trapezoidal accumulator
 // S = Q + f_hat / 2 (Eq. PMLQ: Q^n = S^(n-1) + f_hat^n / 2, S^n = S^(n-1) + f_hat^n), and on P
 // the local part -((sigma_x + sigma_y) f_hat + sigma_x sigma_y Q) of Eq. (pml-general)
@@ -450,18 +460,27 @@ __device__ inline bool outermost(const Geom& g, int x, int y) {
 // the node also stores Q^n in place of S^(n-1) (no kernel of the step reads S^(n-1) after its
 // own node's phase 1; the next step writes S^(n+1) there) and adds its own share
 // +sigma Q_i(x) of the link difference, so phase 2 gathers one value per direction.
-template <class S, class Real, bool DEV, bool STREAM>
+// STAGE (FP32 table-driven launch): S^(n-1) of the node is copied into `stage` (Q values of
+// shared memory owned by this thread) by cp.async while the populations are pulled, instead
+// of being held in registers.
+template <class S, class Real, bool DEV, bool STREAM, bool STAGE = false>
 __device__ __forceinline__ void frame1_node(const Geom& g, const Consts<Real>& c,
                                             const Real* __restrict__ A, Real* __restrict__ B,
                                             Real* __restrict__ Sold,
                                             Real* __restrict__ Snew, double* Uedge,
                                             int save_edges, int* flag, double* Sedge,
-                                            int src_mask, int fi) {
+                                            int src_mask, int fi, Real* stage = nullptr) {
   if (fi >= g.frame_n) return;
   int x, y;
   frame_xy(g, fi, x, y);
   const int d = dist_out(g, x, y);
   const long long idx = gindex(g, x, y);
+  if constexpr (STAGE) {
+    if (pml_node<Real>(g, x, y).has_q) {
+#pragma unroll
+      for (int i = 0; i < S::Q; ++i) cp_async4(stage + i, Sold + (long long)i * g.Sp + fi);
+    }
+  }
   Real p[S::Q];
   load_pop<S, Real, STREAM>(p, A, g, idx);
   const Macro<Real> m = moments<S, Real, DEV>(p, c);
@@ -481,17 +500,18 @@ __device__ __forceinline__ void frame1_node(const Geom& g, const Consts<Real>& c
   if (has_q) {
     // FP32: all accumulator loads in flight before any store (the FP64 build has no registers
     // to spare for them next to its populations)
-    constexpr bool kHoist = sizeof(Real) == 4;
+    constexpr bool kHoist = sizeof(Real) == 4 && !STAGE;
     Real so[S::Q];
     if (kHoist) {
 #pragma unroll
       for (int i = 0; i < S::Q; ++i) so[i] = Sold[(long long)i * g.Sp + fi];
     }
+    if constexpr (STAGE) cp_async_wait_all();
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       const Real eq = eq_dir<S, Real, DEV>(i, m, k, c);
       const Real fhat = eq - c.eqbar[i];
-      const Real s0 = kHoist ? so[i] : Sold[(long long)i * g.Sp + fi];
+      const Real s0 = STAGE ? stage[i] : (kHoist ? so[i] : Sold[(long long)i * g.Sp + fi]);
       const Real q = s0 + Real(0.5) * fhat;
       Snew[(long long)i * g.Sp + fi] = s0 + fhat;
       if (g.link) Sold[(long long)i * g.Sp + fi] = q;   // Q^n over S^(n-1), gathered by phase 2

@@ -249,9 +249,18 @@ __global__ void __launch_bounds__(128) kb_frame1(const MemberDev<Real>* __restri
   const int* e = tab + 2 * blockIdx.x;
   const MemberDev<Real>& md = mem[e[0]];
   const Geom g = md.g;
-  frame1_node<S, Real, DEV, true>(g, md.c, md.A, md.B, md.Sold, md.Snew, md.Uedge_out,
-                                  md.bc.bc == 2 ? 1 : 0, md.flag, md.Sedge_out, md.src_mask,
-                                  e[1] * blockDim.x + threadIdx.x);
+  if constexpr (sizeof(Real) == 4) {
+    // FP32: the node's accumulator is staged in shared memory by cp.async during the pull
+    __shared__ float stage[128 * S::Q];
+    frame1_node<S, Real, DEV, true, true>(g, md.c, md.A, md.B, md.Sold, md.Snew, md.Uedge_out,
+                                          md.bc.bc == 2 ? 1 : 0, md.flag, md.Sedge_out,
+                                          md.src_mask, e[1] * blockDim.x + threadIdx.x,
+                                          reinterpret_cast<Real*>(stage) + threadIdx.x * S::Q);
+  } else {
+    frame1_node<S, Real, DEV, true>(g, md.c, md.A, md.B, md.Sold, md.Snew, md.Uedge_out,
+                                    md.bc.bc == 2 ? 1 : 0, md.flag, md.Sedge_out, md.src_mask,
+                                    e[1] * blockDim.x + threadIdx.x);
+  }
 }
 
 template <class S, class Real>
