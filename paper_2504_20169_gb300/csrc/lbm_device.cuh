@@ -558,11 +558,12 @@ __global__ void __launch_bounds__(128) k_frame1(Geom g, Consts<Real> c, const Re
 // e_i . grad Q_i when sigma_x = sigma_y) with Q = (S^(n-1) + S^n) / 2,
 // Eq. (FD-dx-center) per axis, Eq. (FD-dx-bw) along the outward normal at the outermost layer;
 // with the link gradient, the neighbour's share of the link difference (Q^n read in place).
-template <class S, class Real>
+template <class S, class Real, bool STAGE = false>
 __device__ __forceinline__ void frame2_node(const Geom& g, const Consts<Real>& c,
                                             Real* __restrict__ B, const Real* __restrict__ Sold,
                                             const Real* __restrict__ Snew, double* Sedge,
-                                            int src_mask, int fi) {
+                                            int src_mask, int fi, Real* stq = nullptr,
+                                            Real* stb = nullptr) {
   if (fi >= g.frame_n) return;
   int x, y;
   frame_xy(g, fi, x, y);
@@ -591,23 +592,30 @@ __device__ __forceinline__ void frame2_node(const Geom& g, const Consts<Real>& c
       if (x - R >= g.Lx - g.Fe && x + R < g.Lx && y - R >= g.Fs && y + R < g.Ly - g.Fn) rl = g.Fe;
     }
     double smom[4] = {0.0, 0.0, 0.0, 0.0};   // FP64 sums (cancellation)
-    // every gather (and in FP32 every load of B) in flight before the first update of B
-    constexpr bool kHoistB = sizeof(Real) == 4;
+    // every gather (and in FP32 every load of B) in flight before the first update of B:
+    // in registers, or (STAGE) copied into this thread's shared-memory rows by cp.async
+    constexpr bool kHoistB = sizeof(Real) == 4 && !STAGE;
     Real qg[S::Q], bg[S::Q];
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       if (S::ex(i) == 0 && S::ey(i) == 0) continue;
       const int nb = rl ? fi + S::ey(i) * rl + S::ex(i) : q_slot(g, x + S::ex(i), y + S::ey(i));
-      qg[i] = __ldg(Sold + (long long)i * g.Sp + nb);
-      if (kHoistB) bg[i] = B[(long long)i * g.plane + idx];
+      if constexpr (STAGE) {
+        cp_async4(stq + i, Sold + (long long)i * g.Sp + nb);
+        cp_async4(stb + i, B + (long long)i * g.plane + idx);
+      } else {
+        qg[i] = __ldg(Sold + (long long)i * g.Sp + nb);
+        if (kHoistB) bg[i] = B[(long long)i * g.plane + idx];
+      }
     }
+    if constexpr (STAGE) cp_async_wait_all();
 #pragma unroll
     for (int i = 0; i < S::Q; ++i) {
       if (S::ex(i) == 0 && S::ey(i) == 0) continue;
       const Real* sq = Sold + (long long)i * g.Sp;
-      const Real qn = qg[i];
+      const Real qn = STAGE ? stq[i] : qg[i];
       Real* b = B + (long long)i * g.plane + idx;
-      *b = (kHoistB ? bg[i] : *b) - sx * qn;
+      *b = (STAGE ? stb[i] : (kHoistB ? bg[i] : *b)) - sx * qn;
       if (src) {
         const double part = -double(sx) * (double(qn) - double(__ldg(sq + fi)));
         smom[0] += part;

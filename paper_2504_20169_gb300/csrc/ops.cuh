@@ -264,13 +264,22 @@ __global__ void __launch_bounds__(128) kb_frame1(const MemberDev<Real>* __restri
 }
 
 template <class S, class Real>
-__global__ void __launch_bounds__(128, sizeof(Real) == 4 ? 3 : 2) kb_frame2(const MemberDev<Real>* __restrict__ mem,
+__global__ void __launch_bounds__(128) kb_frame2(const MemberDev<Real>* __restrict__ mem,
                                                  const int* __restrict__ tab) {
   const int* e = tab + 2 * blockIdx.x;
   const MemberDev<Real>& md = mem[e[0]];
   const Geom g = md.g;
-  frame2_node<S, Real>(g, md.c, md.B, md.Sold, md.Snew, md.Sedge_out, md.src_mask,
-                       e[1] * blockDim.x + threadIdx.x);
+  if constexpr (sizeof(Real) == 4) {
+    // FP32: the gathers and the loads of B are staged in shared memory by cp.async
+    __shared__ float stq[128 * S::Q], stb[128 * S::Q];
+    frame2_node<S, Real, true>(g, md.c, md.B, md.Sold, md.Snew, md.Sedge_out, md.src_mask,
+                               e[1] * blockDim.x + threadIdx.x,
+                               reinterpret_cast<Real*>(stq) + threadIdx.x * S::Q,
+                               reinterpret_cast<Real*>(stb) + threadIdx.x * S::Q);
+  } else {
+    frame2_node<S, Real>(g, md.c, md.B, md.Sold, md.Snew, md.Sedge_out, md.src_mask,
+                         e[1] * blockDim.x + threadIdx.x);
+  }
 }
 
 template <class S, class Real, bool DEV>
