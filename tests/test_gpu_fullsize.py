@@ -97,11 +97,13 @@ def test_stress_8192_fp32_runs_and_matches_sampled_oracle_windows():
     assert worst < 1e-5
 
 
-def test_full_grid_elementwise_vs_oracle_at_benchmark_size():
+@pytest.mark.parametrize("grad", ["central", "link"])
+def test_full_grid_elementwise_vs_oracle_at_benchmark_size(grad):
     """Every node of F after 10 steps of the benchmark configuration (2048^2 bulk + PML 32,
-    cubic sigma 0.1, east CBC relax, tau 0.55, Mach 0.3 vortex): interior, frame and boundary
-    kernels and the characteristic targets at their full-size tile and chunk shapes, FP64 and
-    FP32, against one oracle run (about 10 s of CPU per oracle step)."""
+    cubic sigma 0.1, east CBC relax, tau 0.55, Mach 0.3 vortex), with the printed PML gradient
+    and with the link-integrated one: interior, frame and boundary kernels and the
+    characteristic targets at their full-size tile and chunk shapes, FP64 and FP32, against one
+    oracle run (about 10 s of CPU per oracle step)."""
     import os
     from parity_helpers import PERT_TOL, TOL, field_errors
     try:
@@ -114,10 +116,10 @@ def test_full_grid_elementwise_vs_oracle_at_benchmark_size():
     fields = c.fields()
     kw = case_kwargs(nx=c.nx, ny=c.ny, W=c.W, tau=c.tau, sigma_max=c.sigma_max,
                      sigma_power=c.sigma_power, bc=c.bc, nrbc_edges=c.nrbc_edges, beta=c.beta,
-                     mean=c.mean)
+                     mean=c.mean, pml_grad=grad)
     steps = 10
     o = OracleLBM(c.nx, c.ny, c.W, c.tau, c.sigma_max, c.sigma_power, c.bc,
-                  nrbc_edges=c.nrbc_edges, beta=c.beta, mean=c.mean)
+                  nrbc_edges=c.nrbc_edges, beta=c.beta, mean=c.mean, pml_grad=grad)
     o.init(*fields)
     o.step(steps)
     ora = o.fields()
@@ -128,7 +130,7 @@ def test_full_grid_elementwise_vs_oracle_at_benchmark_size():
             s.step(steps)
             gpu = s.moments()
         full, pert = field_errors(gpu, ora)
-        print(f"full grid {precision} full={['%.2e' % e for e in full]} "
+        print(f"full grid {grad} {precision} full={['%.2e' % e for e in full]} "
               f"pert={['%.2e' % e for e in pert]}")
         assert max(full) < TOL[precision], full
         assert max(pert) < PERT_TOL[precision], pert
