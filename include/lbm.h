@@ -49,7 +49,8 @@ typedef enum {
   LBM_ENOMEM = 2,     /* device or pinned allocation failed */
   LBM_ECUDA = 3,      /* a CUDA call failed; lbm_last_error has the message */
   LBM_EUNSTABLE = 4,  /* a non-finite or non-positive density / temperature was produced */
-  LBM_ETIMEOUT = 5,   /* reserved for bounded device-side waits */
+  LBM_ETIMEOUT = 5,   /* reserved: no kernel of this library waits on another, so no call
+                          returns it */
   LBM_ESTATE = 6      /* call not valid in the context's state (e.g. step before init) */
 } lbm_status;
 
